@@ -1,0 +1,149 @@
+/*
+ * ccladder.h -- C ABI of the GB300 (sm_103a) CD-CCSD vvvv ladder library.
+ *
+ * Closed-shell problem statement (arXiv:2202.02019):
+ *   Cholesky integrals (Sec. II.A):        g_acbd = sum_J L^J_ac L^J_bd
+ *   ladder amplitudes:                      tau_ij^cd = t_ij^cd + t_i^c t_j^d
+ *   ladder residual (Sec. II.C, A2 term):   Omega_ij^ab = sum_cd g_acbd tau_ij^cd
+ *   V^4 density (Eq. v4density, App. A):    Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd
+ *   three-index density (Sec. II.D, the V^4 part of W-tilde, built with L):
+ *                                           D^J_ac = sum_bd Gamma_abcd L^J_bd
+ *   Lagrangian slice (Eq. lagrangian):      E = sum_ijab tbar_ij^ab Omega_ij^ab
+ * D carries no factor 2: Eq. (integral_contraction) has the 2, so dE/dL = 2 D.
+ * Neither g nor Gamma is ever stored whole: both are built in tiles of
+ * virtual-pair blocks and consumed at once (Sec. II.C / App. A storage policy),
+ * using the symmetric/antisymmetric pair packing of Sec. II.C.
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers to float64, C-contiguous:
+ *       L_vv  [nj][v][v]    L^J_ac   at (J*v + a)*v + c
+ *       t1    [o][v]        t_i^a    (may be NULL: tau = t2)
+ *       t2    [o][o][v][v]  t_ij^ab  at ((i*o + j)*v + a)*v + b
+ *       tbar2 [o][o][v][v]  same layout as t2
+ *       eps   [o + v]       orbital energies, occupied first
+ *       omega [o][o][v][v]  output, same layout as t2
+ *       D     [nj][v][v]    output, same layout as L_vv
+ *     Kernels do not assume L^J symmetric.  t2 and tbar2 MUST be pair
+ *     symmetric (t_ij^ab = t_ji^ba); the packed algorithm relies on it.
+ *   - Outputs are overwritten, never accumulated into.  The library keeps no
+ *     pointer after return and never allocates or frees device memory: the
+ *     caller owns every buffer, including the workspace `ws` (device, 256-byte
+ *     aligned, at least cc_ladder_workspace_size() bytes).  Calls that share
+ *     a workspace must be ordered on one stream.
+ *   - `stream` is a cudaStream_t (NULL: legacy default stream).  Calls are
+ *     asynchronous; host-detectable argument errors are returned at once,
+ *     device-side errors (bounded waits that gave up) are latched in the
+ *     workspace and reported by cc_ladder_status().  Each call clears the
+ *     latched status at its start, so read it after the call it concerns.
+ *   - n_sys > 1 runs independent systems back to back on `stream`, sharing
+ *     one workspace sized by cc_ladder_workspace_size() over the whole list.
+ *   - Return codes: 0 or a negative CC_ERR_* value; no host aborts, no
+ *     exceptions across the ABI.
+ */
+#ifndef CCLADDER_H
+#define CCLADDER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CC_PREC_FP64 = 0,   /* FP64 operands, FP64 DMMA tensor-core products          */
+  CC_PREC_MIXED = 1   /* 3-piece split-BF16 operands, 6 tcgen05 products per
+                         useful product, FP32 accumulation in TMEM per K-chunk,
+                         FP64 accumulation across chunks and FP64 reductions   */
+} cc_precision;
+
+enum {
+  CC_OK = 0,
+  CC_ERR_ARG = -1,        /* NULL pointer, dims < 1, misaligned, bad n_sys     */
+  CC_ERR_DEVICE = -2,     /* current device is not sm_103                      */
+  CC_ERR_WORKSPACE = -3,  /* ws_bytes smaller than cc_ladder_workspace_size()  */
+  CC_ERR_CUDA = -4,       /* a CUDA call or launch failed (see strerror)       */
+  CC_ERR_TIMEOUT = -5     /* a bounded device wait gave up                     */
+};
+
+/* which-flags for cc_ladder_workspace_size */
+enum {
+  CC_WS_RESIDUAL = 1,
+  CC_WS_DENSITY = 2,
+  CC_WS_LAGRANGIAN = 4,
+  CC_WS_STEP = 7
+};
+
+typedef struct {
+  int32_t o, v, nj;       /* occupied, virtual, Cholesky vectors; all >= 1      */
+  const double* L_vv;     /* [nj][v][v]                                         */
+  const double* t1;       /* [o][v] or NULL                                     */
+  const double* t2;       /* [o][o][v][v], pair symmetric                       */
+  const double* tbar2;    /* [o][o][v][v], pair symmetric; density/lagrangian   */
+  const double* eps;      /* [o+v]; only cc_ladder_update reads it              */
+} cc_ladder_system;
+
+/* Bytes of workspace needed by the calls selected in `which` (CC_WS_* bits)
+ * for this list of systems at precision p.  0 on invalid arguments. */
+size_t cc_ladder_workspace_size(const cc_ladder_system* sys, int n_sys,
+                                cc_precision p, int which);
+
+/* Ladder residual Omega_ij^ab = sum_cd g_acbd tau_ij^cd (Sec. II.C).
+ * omega[s] is a device [o][o][v][v] buffer per system. */
+int cc_ladder_residual(const cc_ladder_system* sys, int n_sys,
+                       double* const* omega, cc_precision p,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Three-index density D^J_ac = sum_bd Gamma_abcd L^J_bd with
+ * Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd (Eq. v4density, Sec. II.D).
+ * D[s] is a device [nj][v][v] buffer per system; requires tbar2. */
+int cc_ladder_density(const cc_ladder_system* sys, int n_sys,
+                      double* const* D, cc_precision p,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* E[s] = sum_ijab tbar_ij^ab Omega_ij^ab (Eq. lagrangian, the ladder slice),
+ * an FP64 reduction written to the device array E[n_sys].  If omega_opt is
+ * non-NULL its buffers hold Omega already (from cc_ladder_residual); if NULL
+ * Omega is computed internally into workspace.  Requires tbar2. */
+int cc_ladder_lagrangian(const cc_ladder_system* sys, int n_sys, double* E,
+                         double* const* omega_opt, cc_precision p,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* One whole pass: Omega, D and E from one shared preparation of L, tau and
+ * tbar (the three calls above fused).  Workspace: CC_WS_STEP. */
+int cc_ladder_step(const cc_ladder_system* sys, int n_sys,
+                   double* const* omega, double* const* D, double* E,
+                   cc_precision p, void* ws, size_t ws_bytes, void* stream);
+
+/* Jacobi amplitude step t'_ij^ab = t_ij^ab + Omega_ij^ab /
+ * (eps_i + eps_j - eps_a - eps_b), in FP64 (the paper leaves the solver
+ * step unstated; this is the orbital-energy-denominator update).
+ * t2_out may equal sys->t2 only if no other call still reads it. */
+int cc_ladder_update(const cc_ladder_system* sys, int n_sys,
+                     double* const* omega, double* const* t2_out,
+                     void* stream);
+
+/* Synchronises `stream`, then returns and clears the device-side status
+ * latched in `ws` by earlier calls (CC_OK or CC_ERR_TIMEOUT), or
+ * CC_ERR_CUDA if the stream reports an error. */
+int cc_ladder_status(void* ws, void* stream);
+
+/* Testing hook for the bounded-wait machinery: launches one kernel that
+ * spins on the device int *flag until it becomes non-zero or `timeout_ns`
+ * nanoseconds pass; on timeout it latches CC_ERR_TIMEOUT in `ws` and
+ * returns.  Read the outcome with cc_ladder_status(). */
+int cc_ladder_debug_wait(const int* flag, long long timeout_ns, void* ws,
+                         void* stream);
+
+/* Static description of a return code; for CC_ERR_CUDA the text of the
+ * last CUDA error seen by the library is appended. */
+const char* cc_ladder_strerror(int code);
+
+/* Kernel launches issued by the calls above since the library was loaded
+ * (a host-side counter). */
+long long cc_ladder_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCLADDER_H */

@@ -1,0 +1,921 @@
+// CD-CCSD vvvv ladder library: workspace planning, preparation / packing
+// kernels, reductions and the C ABI declared in include/ccladder.h.
+//
+// Algorithm (arXiv:2202.02019, closed shell):
+//   Virtual rows are cut into blocks of `s`; a pair block (alpha <= beta)
+//   holds the pairs a<=b with a in block alpha and b in block beta.  Per pair
+//   block, with X^pm_ij = X_ij +- X_ji (Sec. II.C):
+//     g-build   G[(a,c),(b,d)] = sum_J L^J_ac L^J_bd           (Sec. II.A)
+//     pack      g+[ab,cd] = (G_cd + G_dc)(1/2 if c=d), g-[ab,cd] = G_cd - G_dc
+//     ladder    Omega^pm[ab,ij] = sum_{cd} g^pm[ab,cd] tau^pm_ij^cd  (i<=j, c<=d)
+//     unpack    Omega_ij^ab = (Omega+ + Omega-)/2, Omega_ij^ba = (Omega+ - Omega-)/2
+//     Gamma     Gamma'^pm[ab,cd] = sum_ij w^pm_ij tbar^pm_ij^ab tau^pm_ij^cd
+//               (w+ = 1/4 (i=j), 1/2 (i<j); w- = 1/2), Gamma = Gamma'+ + Gamma'-
+//               extended by (anti)symmetry in ab and cd (Eq. v4density)
+//     density   D^J_xc += sum_{y,d} Gamma_xycd L^J_yd   (Sec. II.D, W-tilde)
+//   so that neither g nor Gamma exists beyond one pair block.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ccladder.h"
+#include "gemm.h"
+
+namespace ccl {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
+static std::mutex g_err_mu;
+static std::string g_err_text;
+static void note_cuda(cudaError_t e) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err_text = cudaGetErrorString(e);
+}
+
+static inline int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void decode_sym(int64_t k, int n, int& p, int& q) {
+  int r = 0;
+  while (r + 1 < n && pair_sym(r + 1, r + 1, n) <= k) ++r;
+  p = r;
+  q = static_cast<int>(k - pair_sym(r, r, n)) + r;
+}
+
+// local pair index inside a pair block -> (a_l, b_l)
+__device__ __forceinline__ void pb_pair(int64_t pr, int nb, int diag, int& al, int& bl) {
+  if (!diag) {
+    al = static_cast<int>(pr / nb);
+    bl = static_cast<int>(pr % nb);
+  } else {  // pr = b_l (b_l + 1)/2 + a_l, a_l <= b_l
+    int b = static_cast<int>((sqrt(8.0 * static_cast<double>(pr) + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(b + 1) * (b + 2) / 2 <= pr) ++b;
+    while ((int64_t)b * (b + 1) / 2 > pr) --b;
+    bl = b;
+    al = static_cast<int>(pr - (int64_t)b * (b + 1) / 2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// preparation kernels
+// ---------------------------------------------------------------------------
+// L^J_ac ([nj][v*v]) -> LT[(a,c)][J] (J contiguous, zero for nj <= J < Kj)
+template <typename T>
+__global__ void k_prep_LT(const double* __restrict__ L, int nj, int64_t v2, T* __restrict__ LT, int64_t Kj,
+                          int64_t piece) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int J = j0 + i;
+    const int64_t r = r0 + threadIdx.x;
+    tile[i][threadIdx.x] = (J < nj && r < v2) ? L[static_cast<int64_t>(J) * v2 + r] : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i;
+    const int J = j0 + threadIdx.x;
+    if (r < v2 && J < Kj) Store<T>::put(LT, r * Kj + J, piece, tile[threadIdx.x][i]);
+  }
+}
+
+// L^J_yd -> LN[J][y*vp + d] (zero for d >= v)
+template <typename T>
+__global__ void k_prep_LN(const double* __restrict__ L, int nj, int v, int vp, T* __restrict__ LN, int64_t piece) {
+  const int64_t total = static_cast<int64_t>(nj) * v * vp;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t J = idx / (static_cast<int64_t>(v) * vp);
+    const int64_t rem = idx - J * v * vp;
+    const int y = static_cast<int>(rem / vp), d = static_cast<int>(rem % vp);
+    const double x = d < v ? L[(J * v + y) * v + d] : 0.0;
+    Store<T>::put(LN, idx, piece, x);
+  }
+}
+
+// tau^pm packed, rows = occupied pairs, columns = virtual pairs (K-major for
+// the ladder):  tau+[p+(i,j)][k+(c,d)] = tau_ij^cd + tau_ji^cd   (i<=j, c<=d)
+//               tau-[p-(i,j)][k-(c,d)] = tau_ij^cd - tau_ji^cd   (i<j,  c<d)
+template <typename T>
+__global__ void k_pack_tau(const double* __restrict__ t1, const double* __restrict__ t2, int o, int v,
+                           T* __restrict__ tp, int64_t ldp, int64_t ppiece, T* __restrict__ tm, int64_t ldm,
+                           int64_t mpiece, int minus) {
+  const int c = blockIdx.x;
+  const int64_t pidx = blockIdx.y;
+  int i, j;
+  decode_sym(pidx, o, i, j);
+  const int64_t vv = static_cast<int64_t>(v) * v;
+  const double* tij = t2 + (static_cast<int64_t>(i) * o + j) * vv + static_cast<int64_t>(c) * v;
+  const double* tji = t2 + (static_cast<int64_t>(j) * o + i) * vv + static_cast<int64_t>(c) * v;
+  const double t1ic = t1 ? t1[static_cast<int64_t>(i) * v + c] : 0.0;
+  const double t1jc = t1 ? t1[static_cast<int64_t>(j) * v + c] : 0.0;
+  const int64_t kp0 = pair_sym(c, c, v) - c;
+  const int64_t km0 = (c + 1 < v) ? pair_strict(c, c + 1, v) - (c + 1) : 0;
+  const int64_t pm = (i < j) ? pair_strict(i, j, o) : -1;
+  for (int d = c + threadIdx.x; d < v; d += blockDim.x) {
+    const double a = tij[d] + (t1 ? t1ic * t1[static_cast<int64_t>(j) * v + d] : 0.0);  // tau_ij^cd
+    const double b = tji[d] + (t1 ? t1jc * t1[static_cast<int64_t>(i) * v + d] : 0.0);  // tau_ji^cd
+    Store<T>::put(tp, pidx * ldp + kp0 + d, ppiece, a + b);
+    if (minus && pm >= 0 && d > c) Store<T>::put(tm, pm * ldm + km0 + d, mpiece, a - b);
+  }
+}
+
+// out[c][r] = in[r][c] for r < R, c < C (each split piece moved verbatim)
+template <typename T, int NPc>
+__global__ void k_transpose(const T* __restrict__ in, int64_t R, int64_t C, int64_t ldin, int64_t in_piece,
+                            T* __restrict__ out, int64_t ldout, int64_t out_piece) {
+  __shared__ T tile[NPc][32][33];
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32, r0 = static_cast<int64_t>(blockIdx.y) * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < C)
+#pragma unroll
+      for (int p = 0; p < NPc; ++p) tile[p][i][threadIdx.x] = in[p * in_piece + r * ldin + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < C)
+#pragma unroll
+      for (int p = 0; p < NPc; ++p) out[p * out_piece + c * ldout + r] = tile[p][threadIdx.x][i];
+  }
+}
+
+// tbar^pm rows for the pairs of one pair block, weights of the ij sum folded in:
+//   tbar+[ab][p+(i,j)] = w (tbar_ij^ab + tbar_ji^ab), w = 1/4 (i=j), 1/2 (i<j)
+//   tbar-[ab][p-(i,j)] = 1/2 (tbar_ij^ab - tbar_ji^ab)          (0 for a = b)
+template <typename T>
+__global__ void k_pack_tbar(const double* __restrict__ tb2, int o, int v, int a0, int b0, int nb, int diag,
+                            int64_t pair_off, T* __restrict__ bp, int64_t ldp, int64_t ppiece, T* __restrict__ bm,
+                            int64_t ldm, int64_t mpiece, int minus) {
+  int al, bl;
+  pb_pair(blockIdx.x, nb, diag, al, bl);
+  const int a = a0 + al, b = b0 + bl;
+  const int64_t row = pair_off + blockIdx.x;
+  const int64_t vv = static_cast<int64_t>(v) * v;
+  for (int i = 0; i < o; ++i) {
+    for (int j = i + threadIdx.x; j < o; j += blockDim.x) {
+      const double x = tb2[(static_cast<int64_t>(i) * o + j) * vv + static_cast<int64_t>(a) * v + b];
+      const double y = tb2[(static_cast<int64_t>(j) * o + i) * vv + static_cast<int64_t>(a) * v + b];
+      const double w = (i == j) ? 0.25 : 0.5;
+      Store<T>::put(bp, row * ldp + pair_sym(i, j, o), ppiece, w * (x + y));
+      if (minus && i < j)
+        Store<T>::put(bm, row * ldm + pair_strict(i, j, o), mpiece, (a == b) ? 0.0 : 0.5 * (x - y));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pair-block pack / unpack kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tile_pair(int idx, int nt, int& ct, int& dt) {
+  int r = 0;
+  while (r + 1 < nt && pair_sym(r + 1, r + 1, nt) <= idx) ++r;
+  ct = r;
+  dt = static_cast<int>(idx - pair_sym(r, r, nt)) + r;
+}
+
+// G (FP64, rows (b_l,d), columns (a_l,c), pitch ldG) -> g^pm packed rows
+template <typename T>
+__global__ void k_pack_g(const double* __restrict__ G, int64_t ldG, int v, int a0, int b0, int nb, int diag, int nt,
+                         T* __restrict__ gp, int64_t ldp, int64_t ppiece, T* __restrict__ gm, int64_t ldm,
+                         int64_t mpiece, int minus) {
+  __shared__ double s1[32][33];  // s1[dd][cc] = G^{ab}_{c,d}
+  __shared__ double s2[32][33];  // s2[cc][dd] = G^{ab}_{d,c}
+  const int64_t pr = blockIdx.y;
+  int al, bl;
+  pb_pair(pr, nb, diag, al, bl);
+  int ct, dt;
+  tile_pair(blockIdx.x, nt, ct, dt);
+  const int c0 = ct * 32, d0 = dt * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t colA = static_cast<int64_t>(al) * v;
+  const int64_t rowB = static_cast<int64_t>(bl) * v;
+  for (int r = ty; r < 32; r += 8) {
+    const int d = d0 + r, c = c0 + tx;
+    s1[r][tx] = (c < v && d < v) ? G[(rowB + d) * ldG + colA + c] : 0.0;
+    const int c2 = c0 + r, d2 = d0 + tx;
+    s2[r][tx] = (c2 < v && d2 < v) ? G[(rowB + c2) * ldG + colA + d2] : 0.0;
+  }
+  __syncthreads();
+  const bool same = (a0 + al) == (b0 + bl);
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r, d = d0 + tx;
+    if (c >= v || d >= v || d < c) continue;
+    const double gcd = s1[tx][r], gdc = s2[r][tx];
+    Store<T>::put(gp, pr * ldp + pair_sym(c, d, v), ppiece, (c == d) ? gcd : gcd + gdc);
+    if (minus && c < d) Store<T>::put(gm, pr * ldm + pair_strict(c, d, v), mpiece, same ? 0.0 : gcd - gdc);
+  }
+}
+
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  x = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  }
+  return x;  // valid in thread 0
+}
+
+// Omega^pm [occupied pair][local pair] -> Omega_ij^ab (and/or the E partial)
+__global__ void k_unpack_omega(const double* __restrict__ Op, const double* __restrict__ Om, int64_t ldO, int o,
+                               int v, int a0, int b0, int nb, int diag, int64_t npairs, int minus,
+                               double* __restrict__ omega, const double* __restrict__ tbar2,
+                               double* __restrict__ epart) {
+  const int i = blockIdx.x / o, j = blockIdx.x % o;
+  const int lo = min(i, j), hi = max(i, j);
+  const int64_t pp = pair_sym(lo, hi, o);
+  const int64_t pm = (i != j) ? pair_strict(lo, hi, o) : -1;
+  const double sg = (i < j) ? 1.0 : -1.0;
+  const int64_t base = (static_cast<int64_t>(i) * o + j) * v * v;
+  double esum = 0.0;
+  for (int64_t pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+    int al, bl;
+    pb_pair(pr, nb, diag, al, bl);
+    const int a = a0 + al, b = b0 + bl;
+    const double P = Op[pp * ldO + pr];
+    const double M = (minus && pm >= 0) ? sg * Om[pm * ldO + pr] : 0.0;
+    const double wab = 0.5 * (P + M), wba = 0.5 * (P - M);
+    const int64_t iab = base + static_cast<int64_t>(a) * v + b, iba = base + static_cast<int64_t>(b) * v + a;
+    if (omega) {
+      omega[iab] = wab;
+      if (a != b) omega[iba] = wba;
+    }
+    if (epart) {
+      esum += tbar2[iab] * wab;
+      if (a != b) esum += tbar2[iba] * wba;
+    }
+  }
+  if (epart) {
+    const double s = block_sum(esum);
+    if (threadIdx.x == 0) epart[blockIdx.x] = s;
+  }
+}
+
+// Gamma'^pm [local pair][virtual pair] -> full Gamma^{xy}_{cd} slabs:
+//   top[(x_l v + c)][(y_l vp + d)]  x in block alpha, y in block beta
+//   bot[(x_l v + c)][(y_l vp + d)]  x in block beta,  y in block alpha
+// Gamma_abcd = P(cd) + sgn(c,d) M(cd) for the stored pair (a<=b),
+// Gamma_bacd = P(cd) - sgn(c,d) M(cd); P symmetric, M antisymmetric in cd.
+template <typename T>
+__global__ void k_unpack_gamma(const double* __restrict__ Gp, const double* __restrict__ Gm, int64_t ldp,
+                               int64_t ldm, int v, int vp, int a0, int b0, int nb, int diag, int nt, int minus,
+                               T* __restrict__ top, int64_t ldt, int64_t tpiece, T* __restrict__ bot, int64_t ldb,
+                               int64_t bpiece) {
+  __shared__ double sP[32][33], sM[32][33];  // [c - c0][d - d0], c <= d
+  const int64_t pr = blockIdx.y;
+  int al, bl;
+  pb_pair(pr, nb, diag, al, bl);
+  int ct, dt;
+  tile_pair(blockIdx.x, nt, ct, dt);
+  const int c0 = ct * 32, d0 = dt * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r, d = d0 + tx;
+    const bool in = c < v && d < v && c <= d;
+    sP[r][tx] = in ? Gp[pr * ldp + pair_sym(c, d, v)] : 0.0;
+    sM[r][tx] = (in && minus && c < d) ? Gm[pr * ldm + pair_strict(c, d, v)] : 0.0;
+  }
+  __syncthreads();
+  const bool same = (a0 + al) == (b0 + bl);
+  // ordered pairs (x, y): (a, b) with sign +1, (b, a) with sign -1
+  for (int which = 0; which < 2; ++which) {
+    if (which == 1 && same) break;
+    const double sp = which == 0 ? 1.0 : -1.0;
+    T* dst;
+    int64_t ld, piece, xrow, ycol;
+    if (which == 0) {
+      dst = top; ld = ldt; piece = tpiece;
+      xrow = static_cast<int64_t>(al) * v; ycol = static_cast<int64_t>(bl) * vp;
+    } else if (diag) {
+      dst = top; ld = ldt; piece = tpiece;
+      xrow = static_cast<int64_t>(bl) * v; ycol = static_cast<int64_t>(al) * vp;
+    } else {
+      dst = bot; ld = ldb; piece = bpiece;
+      xrow = static_cast<int64_t>(bl) * v; ycol = static_cast<int64_t>(al) * vp;
+    }
+    // the tile itself (rows in ct, cols in dt) and, off the diagonal, its mirror
+    for (int mirror = 0; mirror < (ct == dt ? 1 : 2); ++mirror) {
+      const int R0 = mirror ? d0 : c0, W0 = mirror ? c0 : d0;
+      for (int r = ty; r < 32; r += 8) {
+        const int row = R0 + r, col = W0 + tx;
+        if (row >= v || col >= v) continue;
+        const int lo = min(row, col), hi = max(row, col);
+        const double P = sP[lo - c0][hi - d0];
+        const double M = sM[lo - c0][hi - d0];
+        const double sgn = row < col ? 1.0 : (row > col ? -1.0 : 0.0);
+        Store<T>::put(dst, (xrow + row) * ld + ycol + col, piece, P + sp * sgn * M);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reductions, update, debug wait
+// ---------------------------------------------------------------------------
+__global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                              double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    s += x[k] * y[k];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s += part[k];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_update(const double* __restrict__ t2, const double* __restrict__ om, const double* __restrict__ eps,
+                         int o, int v, double* __restrict__ out) {
+  const int64_t total = static_cast<int64_t>(o) * o * v * v;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(k % v);
+    const int a = static_cast<int>((k / v) % v);
+    const int j = static_cast<int>((k / (static_cast<int64_t>(v) * v)) % o);
+    const int i = static_cast<int>(k / (static_cast<int64_t>(v) * v * o));
+    const double den = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+    out[k] = t2[k] + om[k] / den;
+  }
+}
+
+__global__ void k_debug_wait(const int* flag, unsigned long long timeout_ns, Status* st) {
+  const volatile int* f = flag;
+  const uint64_t t0 = globaltimer();
+  while (*f == 0) {
+    if (globaltimer() - t0 > timeout_ns) {
+      latch_error(st, kErrTimeout, 900);
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+struct PBlock {
+  int a0, na, b0, nb, diag;
+  int64_t npairs, pair_off;
+};
+
+struct Plan {
+  int o = 0, v = 0, nj = 0, prec = 0;
+  int vp = 0, s = 0, nblk = 0, nt = 0;
+  int minus = 0;
+  int64_t Pvp = 0, Pvm = 0, Pop = 0, Pom = 0;
+  int64_t Kj = 0, Kvp = 0, Kvm = 0, Kop = 0, Kom = 0;
+  std::vector<PBlock> pbs;
+  int64_t maxpairs = 0, maxrows = 0, ldO = 0, ldt = 0;
+  int64_t kchunk = 0;
+  int64_t n_epart = 0;
+  // byte offsets into the workspace; SIZE_MAX = not present
+  size_t o_LT = 0, o_LN = 0, o_tp = 0, o_tm = 0, o_tpT = 0, o_tmT = 0, o_bp = 0, o_bm = 0;
+  size_t o_G = 0, o_gp = 0, o_gm = 0, o_Op = 0, o_Om = 0, o_Gp = 0, o_Gm = 0, o_Gt = 0, o_Gb = 0, o_E = 0;
+  size_t total = 0;
+};
+
+constexpr size_t kStatusBytes = 256;
+
+static int env_int(const char* name, int dflt) {
+  const char* s = std::getenv(name);
+  if (!s || !*s) return dflt;
+  return std::atoi(s);
+}
+
+// bytes of an R x C matrix in the path's element format
+static size_t mat_bytes(int prec, int64_t R, int64_t C) {
+  return static_cast<size_t>(R) * static_cast<size_t>(C) * (prec == CC_PREC_MIXED ? 6 : 8);
+}
+
+static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) {
+  const int64_t o = sy.o, v = sy.v, nj = sy.nj;
+  P.o = sy.o; P.v = sy.v; P.nj = sy.nj; P.prec = prec;
+  P.vp = static_cast<int>(rup(v, 8));
+  P.Pvp = v * (v + 1) / 2; P.Pvm = v * (v - 1) / 2;
+  P.Pop = o * (o + 1) / 2; P.Pom = o * (o - 1) / 2;
+  P.minus = (P.Pvm > 0 && P.Pom > 0) ? 1 : 0;
+  P.Kj = rup(nj, 32);
+  P.Kvp = rup(P.Pvp, 32); P.Kvm = rup(P.Pvm, 32);
+  P.Kop = rup(P.Pop, 32); P.Kom = rup(P.Pom, 32);
+  int s = env_int("CC_BLOCK", 32);
+  s = std::max(4, (s / 4) * 4);
+  s = static_cast<int>(std::min<int64_t>(s, rup(v, 4)));
+  P.s = s;
+  P.nblk = static_cast<int>((v + s - 1) / s);
+  P.nt = static_cast<int>((v + 31) / 32);
+  P.kchunk = rup(std::max(32, env_int("CC_KCHUNK", prec == CC_PREC_MIXED ? 4096 : 1 << 30)), 32);
+  P.pbs.clear();
+  int64_t off = 0;
+  for (int al = 0; al < P.nblk; ++al)
+    for (int be = al; be < P.nblk; ++be) {
+      PBlock b;
+      b.a0 = al * s; b.na = static_cast<int>(std::min<int64_t>(s, v - b.a0));
+      b.b0 = be * s; b.nb = static_cast<int>(std::min<int64_t>(s, v - b.b0));
+      b.diag = al == be;
+      b.npairs = b.diag ? (int64_t)b.na * (b.na + 1) / 2 : (int64_t)b.na * b.nb;
+      b.pair_off = off;
+      off += b.npairs;
+      P.pbs.push_back(b);
+      P.maxpairs = std::max(P.maxpairs, b.npairs);
+    }
+  if (off != P.Pvp) return false;
+  if (P.maxpairs > 65535 || P.Pop > 65535) return false;  // grid.y limits of the pack kernels
+  P.maxrows = static_cast<int64_t>(s) * v;
+  P.ldO = rup(P.maxpairs, 2);
+  P.ldt = static_cast<int64_t>(s) * P.vp;
+  P.n_epart = std::max<int64_t>(1024, static_cast<int64_t>(P.pbs.size()) * o * o);
+
+  const bool res = which & (CC_WS_RESIDUAL | CC_WS_LAGRANGIAN);
+  const bool den = which & CC_WS_DENSITY;
+  size_t cur = kStatusBytes;
+  auto take = [&](size_t bytes) {
+    const size_t at = cur;
+    cur += rup(static_cast<int64_t>(bytes), 256);
+    return at;
+  };
+  const int pr = prec;
+  P.o_tp = take(mat_bytes(pr, P.Pop, P.Kvp));
+  P.o_tm = take(mat_bytes(pr, P.Pom, P.Kvm));
+  if (res) {
+    P.o_LT = take(mat_bytes(pr, v * v, P.Kj));
+    P.o_G = take(static_cast<size_t>(P.maxrows) * P.maxrows * 8);
+    P.o_gp = take(mat_bytes(pr, P.maxpairs, P.Kvp));
+    P.o_gm = take(mat_bytes(pr, P.maxpairs, P.Kvm));
+    P.o_Op = take(static_cast<size_t>(P.Pop) * P.ldO * 8);
+    P.o_Om = take(static_cast<size_t>(P.Pom) * P.ldO * 8);
+  }
+  if (den) {
+    P.o_LN = take(mat_bytes(pr, nj, v * P.vp));
+    P.o_tpT = take(mat_bytes(pr, P.Pvp, P.Kop));
+    P.o_tmT = take(mat_bytes(pr, P.Pvm, P.Kom));
+    P.o_bp = take(mat_bytes(pr, P.Pvp, P.Kop));
+    P.o_bm = take(mat_bytes(pr, P.Pvp, P.Kom));
+    P.o_Gp = take(static_cast<size_t>(P.maxpairs) * P.Kvp * 8);
+    P.o_Gm = take(static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
+    P.o_Gt = take(mat_bytes(pr, P.maxrows, P.ldt));
+    P.o_Gb = take(mat_bytes(pr, P.maxrows, P.ldt));
+  }
+  P.o_E = take(static_cast<size_t>(P.n_epart) * 8);
+  P.total = cur;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// execution
+// ---------------------------------------------------------------------------
+struct Ctx {
+  cudaStream_t st;
+  Status* status;
+  uint64_t timeout_ns;
+  int err = 0;
+  void check(int rc) {
+    if (rc && !err) err = rc;
+  }
+  void cuda(cudaError_t e) {
+    if (e != cudaSuccess && !err) {
+      note_cuda(e);
+      err = CC_ERR_CUDA;
+    }
+  }
+  void launched(int n = 1) {
+    count_launch(n);
+    cuda(cudaPeekAtLastError());
+  }
+};
+
+template <typename T>
+struct Path;
+template <>
+struct Path<double> {
+  static constexpr int NP = 1;
+  static int gemm(const GemmOp& g, cudaStream_t s) { return gemm_f64(g, s); }
+};
+template <>
+struct Path<__nv_bfloat16> {
+  static constexpr int NP = 3;
+  static int gemm(const GemmOp& g, cudaStream_t s) { return gemm_mixed(g, s); }
+};
+
+template <typename T>
+static T* at(char* ws, size_t off) {
+  return reinterpret_cast<T*>(ws + off);
+}
+
+template <typename T>
+static GemmOp mk_gemm(const T* A, int64_t lda, int64_t a_rows, int64_t a_cols, int64_t a_piece, const T* B,
+                      int64_t ldb, int64_t b_rows, int64_t b_cols, int64_t b_piece, int64_t M, int64_t N, int64_t K,
+                      double* out, int64_t ldo, int atomic, int64_t kchunk, const Ctx& c) {
+  GemmOp g;
+  g.A = A; g.lda = lda; g.a_rows = a_rows; g.a_cols = a_cols; g.a_piece = a_piece;
+  g.B = B; g.ldb = ldb; g.b_rows = b_rows; g.b_cols = b_cols; g.b_piece = b_piece;
+  g.M = M; g.N = N; g.K = K; g.out = out; g.ldo = ldo; g.atomic = atomic; g.kchunk = kchunk;
+  g.status = c.status; g.timeout_ns = c.timeout_ns;
+  return g;
+}
+
+// K chunk for one contraction: the precision bound of the path, shrunk when
+// needed so that the launch has at least ~2 waves of CTAs on 152 SMs.
+static int64_t pick_kchunk(const Plan& P, int64_t M, int64_t N, int64_t K, bool want_split) {
+  int64_t kc = std::min<int64_t>(P.kchunk, K);
+  if (!want_split) return kc;
+  const int64_t bm = P.prec == CC_PREC_MIXED ? 128 : 64, bn = P.prec == CC_PREC_MIXED ? 128 : 64;
+  const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+  const int64_t target = 2 * 152;
+  if (tiles < target) {
+    const int64_t splits = std::min<int64_t>((target + tiles - 1) / tiles, std::max<int64_t>(1, K / 256));
+    kc = std::min(kc, rup((K + splits - 1) / splits, 32));
+  }
+  return std::max<int64_t>(32, kc);
+}
+
+template <typename T>
+static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, double* omega, double* D, double* E,
+                       bool do_res, bool do_den, bool do_E, Ctx& c) {
+  const int o = P.o, v = P.v, nj = P.nj, vp = P.vp;
+  const int64_t vv = static_cast<int64_t>(v) * v;
+  const int minus = P.minus;
+  cudaStream_t st = c.st;
+  T* tp = at<T>(ws, P.o_tp);
+  T* tm = at<T>(ws, P.o_tm);
+  const int64_t tp_piece = P.Pop * P.Kvp, tm_piece = P.Pom * P.Kvm;
+
+  // --- tau^pm (both directions need it)
+  c.cuda(cudaMemsetAsync(tp, 0, mat_bytes(P.prec, P.Pop, P.Kvp), st));
+  if (minus) c.cuda(cudaMemsetAsync(tm, 0, mat_bytes(P.prec, P.Pom, P.Kvm), st));
+  k_pack_tau<T><<<dim3(v, static_cast<unsigned>(P.Pop)), 128, 0, st>>>(sy.t1, sy.t2, o, v, tp, P.Kvp, tp_piece, tm,
+                                                                      P.Kvm, tm_piece, minus);
+  c.launched();
+
+  double* epart = at<double>(ws, P.o_E);
+  const int64_t o2 = static_cast<int64_t>(o) * o;
+
+  // --- residual-side preparation
+  T *LT = nullptr, *gp = nullptr, *gm = nullptr;
+  double *G = nullptr, *Op = nullptr, *Om = nullptr;
+  int64_t LT_piece = vv * P.Kj, g_piece_p = P.maxpairs * P.Kvp, g_piece_m = P.maxpairs * P.Kvm;
+  if (do_res) {
+    LT = at<T>(ws, P.o_LT);
+    G = at<double>(ws, P.o_G);
+    gp = at<T>(ws, P.o_gp);
+    gm = at<T>(ws, P.o_gm);
+    Op = at<double>(ws, P.o_Op);
+    Om = at<double>(ws, P.o_Om);
+    k_prep_LT<T><<<dim3(static_cast<unsigned>((vv + 31) / 32), static_cast<unsigned>(P.Kj / 32)), dim3(32, 8), 0,
+                   st>>>(sy.L_vv, nj, vv, LT, P.Kj, LT_piece);
+    c.launched();
+    c.cuda(cudaMemsetAsync(gp, 0, mat_bytes(P.prec, P.maxpairs, P.Kvp), st));
+    if (minus) c.cuda(cudaMemsetAsync(gm, 0, mat_bytes(P.prec, P.maxpairs, P.Kvm), st));
+  }
+
+  // --- density-side preparation
+  T *LN = nullptr, *tpT = nullptr, *tmT = nullptr, *bp = nullptr, *bm = nullptr, *Gt = nullptr, *Gb = nullptr;
+  double *Gp = nullptr, *Gm = nullptr;
+  const int64_t LN_piece = static_cast<int64_t>(nj) * v * vp;
+  const int64_t tpT_piece = P.Pvp * P.Kop, tmT_piece = P.Pvm * P.Kom;
+  const int64_t bp_piece = P.Pvp * P.Kop, bm_piece = P.Pvp * P.Kom;
+  const int64_t gt_piece = P.maxrows * P.ldt;
+  if (do_den) {
+    LN = at<T>(ws, P.o_LN);
+    tpT = at<T>(ws, P.o_tpT);
+    tmT = at<T>(ws, P.o_tmT);
+    bp = at<T>(ws, P.o_bp);
+    bm = at<T>(ws, P.o_bm);
+    Gp = at<double>(ws, P.o_Gp);
+    Gm = at<double>(ws, P.o_Gm);
+    Gt = at<T>(ws, P.o_Gt);
+    Gb = at<T>(ws, P.o_Gb);
+    k_prep_LN<T><<<2048, 256, 0, st>>>(sy.L_vv, nj, v, vp, LN, LN_piece);
+    c.launched();
+    c.cuda(cudaMemsetAsync(tpT, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
+    k_transpose<T, Path<T>::NP><<<dim3(static_cast<unsigned>((P.Pvp + 31) / 32), static_cast<unsigned>((P.Pop + 31) / 32)),
+                                  dim3(32, 8), 0, st>>>(tp, P.Pop, P.Pvp, P.Kvp, tp_piece, tpT, P.Kop, tpT_piece);
+    c.launched();
+    c.cuda(cudaMemsetAsync(bp, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
+    if (minus) {
+      c.cuda(cudaMemsetAsync(tmT, 0, mat_bytes(P.prec, P.Pvm, P.Kom), st));
+      k_transpose<T, Path<T>::NP><<<dim3(static_cast<unsigned>((P.Pvm + 31) / 32), static_cast<unsigned>((P.Pom + 31) / 32)),
+                                    dim3(32, 8), 0, st>>>(tm, P.Pom, P.Pvm, P.Kvm, tm_piece, tmT, P.Kom, tmT_piece);
+      c.launched();
+      c.cuda(cudaMemsetAsync(bm, 0, mat_bytes(P.prec, P.Pvp, P.Kom), st));
+    }
+    for (const PBlock& b : P.pbs) {
+      k_pack_tbar<T><<<static_cast<unsigned>(b.npairs), 128, 0, st>>>(sy.tbar2, o, v, b.a0, b.b0, b.nb, b.diag,
+                                                                     b.pair_off, bp, P.Kop, bp_piece, bm, P.Kom,
+                                                                     bm_piece, minus);
+      c.launched();
+    }
+    c.cuda(cudaMemsetAsync(Gt, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
+    c.cuda(cudaMemsetAsync(Gb, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
+    c.cuda(cudaMemsetAsync(D, 0, static_cast<size_t>(nj) * vv * 8, st));
+  }
+
+  const unsigned ntp = static_cast<unsigned>(P.nt * (P.nt + 1) / 2);
+  for (size_t ib = 0; ib < P.pbs.size() && !c.err; ++ib) {
+    const PBlock& b = P.pbs[ib];
+    if (do_res) {
+      // g-build: G[(b_l,d)][(a_l,c)] = sum_J L^J_ac L^J_bd
+      const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
+      const int64_t kc = pick_kchunk(P, M, N, P.Kj, false);
+      if (kc < P.Kj) c.cuda(cudaMemsetAsync(G, 0, static_cast<size_t>(M) * N * 8, st));
+      c.check(Path<T>::gemm(mk_gemm<T>(LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, LT_piece,
+                                       LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, LT_piece, M, N,
+                                       P.Kj, G, M, 0, kc, c),
+                            st));
+      k_pack_g<T><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
+          G, M, v, b.a0, b.b0, b.nb, b.diag, P.nt, gp, P.Kvp, g_piece_p, gm, P.Kvm, g_piece_m, minus);
+      c.launched();
+      // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]
+      c.cuda(cudaMemsetAsync(Op, 0, static_cast<size_t>(P.Pop) * P.ldO * 8, st));
+      c.check(Path<T>::gemm(mk_gemm<T>(gp, P.Kvp, b.npairs, P.Kvp, g_piece_p, tp, P.Kvp, P.Pop, P.Kvp, tp_piece,
+                                       b.npairs, P.Pop, P.Kvp, Op, P.ldO, 1,
+                                       pick_kchunk(P, b.npairs, P.Pop, P.Kvp, true), c),
+                            st));
+      if (minus) {
+        c.cuda(cudaMemsetAsync(Om, 0, static_cast<size_t>(P.Pom) * P.ldO * 8, st));
+        c.check(Path<T>::gemm(mk_gemm<T>(gm, P.Kvm, b.npairs, P.Kvm, g_piece_m, tm, P.Kvm, P.Pom, P.Kvm, tm_piece,
+                                         b.npairs, P.Pom, P.Kvm, Om, P.ldO, 1,
+                                         pick_kchunk(P, b.npairs, P.Pom, P.Kvm, true), c),
+                              st));
+      }
+      k_unpack_omega<<<static_cast<unsigned>(o2), 256, 0, st>>>(
+          Op, Om, P.ldO, o, v, b.a0, b.b0, b.nb, b.diag, b.npairs, minus, omega, sy.tbar2,
+          do_E ? epart + static_cast<int64_t>(ib) * o2 : nullptr);
+      c.launched();
+    }
+    if (do_den) {
+      // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]
+      {
+        const int64_t kc = pick_kchunk(P, P.Pvp, b.npairs, P.Kop, false);
+        if (kc < P.Kop) c.cuda(cudaMemsetAsync(Gp, 0, static_cast<size_t>(b.npairs) * P.Kvp * 8, st));
+        c.check(Path<T>::gemm(mk_gemm<T>(tpT, P.Kop, P.Pvp, P.Kop, tpT_piece, bp + b.pair_off * P.Kop, P.Kop,
+                                         b.npairs, P.Kop, bp_piece, P.Pvp, b.npairs, P.Kop, Gp, P.Kvp, 0, kc, c),
+                              st));
+      }
+      if (minus) {
+        const int64_t kc = pick_kchunk(P, P.Pvm, b.npairs, P.Kom, false);
+        if (kc < P.Kom) c.cuda(cudaMemsetAsync(Gm, 0, static_cast<size_t>(b.npairs) * P.Kvm * 8, st));
+        c.check(Path<T>::gemm(mk_gemm<T>(tmT, P.Kom, P.Pvm, P.Kom, tmT_piece, bm + b.pair_off * P.Kom, P.Kom,
+                                         b.npairs, P.Kom, bm_piece, P.Pvm, b.npairs, P.Kom, Gm, P.Kvm, 0, kc, c),
+                              st));
+      }
+      k_unpack_gamma<T><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
+          Gp, Gm, P.Kvp, P.Kvm, v, vp, b.a0, b.b0, b.nb, b.diag, P.nt, minus, Gt, P.ldt, gt_piece, Gb, P.ldt,
+          gt_piece);
+      c.launched();
+      // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd
+      {
+        const int64_t M = static_cast<int64_t>(b.na) * v, K = rup(static_cast<int64_t>(b.nb) * vp, 32);
+        c.check(Path<T>::gemm(mk_gemm<T>(Gt, P.ldt, M, P.ldt, gt_piece, LN + static_cast<int64_t>(b.b0) * vp,
+                                         static_cast<int64_t>(v) * vp, nj,
+                                         static_cast<int64_t>(v - b.b0) * vp, LN_piece, M, nj, K,
+                                         D + static_cast<int64_t>(b.a0) * v, vv, 1, pick_kchunk(P, M, nj, K, true), c),
+                              st));
+      }
+      if (!b.diag) {
+        const int64_t M = static_cast<int64_t>(b.nb) * v, K = rup(static_cast<int64_t>(b.na) * vp, 32);
+        c.check(Path<T>::gemm(mk_gemm<T>(Gb, P.ldt, M, P.ldt, gt_piece, LN + static_cast<int64_t>(b.a0) * vp,
+                                         static_cast<int64_t>(v) * vp, nj,
+                                         static_cast<int64_t>(v - b.a0) * vp, LN_piece, M, nj, K,
+                                         D + static_cast<int64_t>(b.b0) * v, vv, 1, pick_kchunk(P, M, nj, K, true), c),
+                              st));
+      }
+    }
+  }
+  if (do_E && do_res) {
+    k_sum_final<<<1, 1024, 0, st>>>(epart, static_cast<int64_t>(P.pbs.size()) * o2, E);
+    c.launched();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+static int check_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CC_ERR_DEVICE;
+  int maj = 0, min_ = 0;
+  if (cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return CC_ERR_DEVICE;
+  if (cudaDeviceGetAttribute(&min_, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return CC_ERR_DEVICE;
+  return (maj == 10 && min_ == 3) ? CC_OK : CC_ERR_DEVICE;
+}
+
+static bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
+static int validate(const cc_ladder_system* sys, int n_sys, bool need_tbar) {
+  if (!sys || n_sys < 1) return CC_ERR_ARG;
+  for (int i = 0; i < n_sys; ++i) {
+    const cc_ladder_system& s = sys[i];
+    if (s.o < 1 || s.v < 1 || s.nj < 1) return CC_ERR_ARG;
+    if (!s.L_vv || !s.t2) return CC_ERR_ARG;
+    if (need_tbar && !s.tbar2) return CC_ERR_ARG;
+    if (!aligned8(s.L_vv) || !aligned8(s.t2) || !aligned8(s.t1) || !aligned8(s.tbar2) || !aligned8(s.eps))
+      return CC_ERR_ARG;
+  }
+  return CC_OK;
+}
+
+static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int which) {
+  size_t need = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    Plan P;
+    if (!make_plan(sys[i], prec, which, P)) return 0;
+    need = std::max(need, P.total);
+  }
+  return need;
+}
+
+static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
+               int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream) {
+  if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED) return CC_ERR_ARG;
+  int rc = validate(sys, n_sys, den || want_E);
+  if (rc) return rc;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  for (int i = 0; i < n_sys; ++i) {
+    if (res && omega && !omega[i] && !want_E) return CC_ERR_ARG;
+    if (res && omega && omega[i] && !aligned8(omega[i])) return CC_ERR_ARG;
+    if (den && (!D || !D[i] || !aligned8(D[i]))) return CC_ERR_ARG;
+  }
+  if (want_E && (!E || !aligned8(E))) return CC_ERR_ARG;
+  if ((rc = check_device())) return rc;
+  const size_t need = ws_need(sys, n_sys, prec, which);
+  if (!need) return CC_ERR_ARG;
+  if (ws_bytes < need) return CC_ERR_WORKSPACE;
+  Ctx c;
+  c.st = static_cast<cudaStream_t>(stream);
+  c.status = reinterpret_cast<Status*>(ws);
+  c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
+  // every call starts from a clear status word; cc_ladder_status() reads it
+  c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), c.st));
+  for (int i = 0; i < n_sys && !c.err; ++i) {
+    Plan P;
+    make_plan(sys[i], prec, which, P);
+    double* om = (res && omega) ? omega[i] : nullptr;
+    double* Dd = den ? D[i] : nullptr;
+    double* Ei = want_E ? E + i : nullptr;
+    if (prec == CC_PREC_MIXED)
+      run_system<__nv_bfloat16>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
+    else
+      run_system<double>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
+  }
+  return c.err;
+}
+
+}  // namespace ccl
+
+using namespace ccl;
+
+extern "C" {
+
+size_t cc_ladder_workspace_size(const cc_ladder_system* sys, int n_sys, cc_precision p, int which) {
+  if (validate(sys, n_sys, false) || (p != CC_PREC_FP64 && p != CC_PREC_MIXED) || !(which & CC_WS_STEP)) return 0;
+  return ws_need(sys, n_sys, p, which);
+}
+
+int cc_ladder_residual(const cc_ladder_system* sys, int n_sys, double* const* omega, cc_precision p, void* ws,
+                       size_t ws_bytes, void* stream) {
+  if (!omega) return CC_ERR_ARG;
+  for (int i = 0; sys && i < n_sys; ++i)
+    if (!omega[i]) return CC_ERR_ARG;
+  return run(sys, n_sys, omega, nullptr, nullptr, p, CC_WS_RESIDUAL, true, false, false, ws, ws_bytes, stream);
+}
+
+int cc_ladder_density(const cc_ladder_system* sys, int n_sys, double* const* D, cc_precision p, void* ws,
+                      size_t ws_bytes, void* stream) {
+  if (!D) return CC_ERR_ARG;
+  return run(sys, n_sys, nullptr, D, nullptr, p, CC_WS_DENSITY, false, true, false, ws, ws_bytes, stream);
+}
+
+int cc_ladder_lagrangian(const cc_ladder_system* sys, int n_sys, double* E, double* const* omega_opt, cc_precision p,
+                         void* ws, size_t ws_bytes, void* stream) {
+  if (omega_opt == nullptr)
+    return run(sys, n_sys, nullptr, nullptr, E, p, CC_WS_LAGRANGIAN, true, false, true, ws, ws_bytes, stream);
+  // Omega given: plain FP64 reduction sum tbar * Omega
+  int rc = validate(sys, n_sys, true);
+  if (rc) return rc;
+  if (!E || !aligned8(E) || !ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  if ((rc = check_device())) return rc;
+  if (ws_bytes < kStatusBytes + 1024 * 8) return CC_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + kStatusBytes);
+  if (cudaMemsetAsync(ws, 0, sizeof(Status), st) != cudaSuccess) return CC_ERR_CUDA;
+  for (int i = 0; i < n_sys; ++i) {
+    if (!omega_opt[i] || !aligned8(omega_opt[i])) return CC_ERR_ARG;
+    const int64_t n = static_cast<int64_t>(sys[i].o) * sys[i].o * sys[i].v * sys[i].v;
+    k_dot_partial<<<1024, 256, 0, st>>>(sys[i].tbar2, omega_opt[i], n, part);
+    k_sum_final<<<1, 1024, 0, st>>>(part, 1024, E + i);
+    count_launch(2);
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+      note_cuda(e);
+      return CC_ERR_CUDA;
+    }
+  }
+  return CC_OK;
+}
+
+int cc_ladder_step(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
+                   cc_precision p, void* ws, size_t ws_bytes, void* stream) {
+  if (!omega || !D || !E) return CC_ERR_ARG;
+  for (int i = 0; sys && i < n_sys; ++i)
+    if (!omega[i]) return CC_ERR_ARG;
+  return run(sys, n_sys, omega, D, E, p, CC_WS_STEP, true, true, true, ws, ws_bytes, stream);
+}
+
+int cc_ladder_update(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* t2_out,
+                     void* stream) {
+  int rc = validate(sys, n_sys, false);
+  if (rc) return rc;
+  if (!omega || !t2_out) return CC_ERR_ARG;
+  if ((rc = check_device())) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n_sys; ++i) {
+    if (!sys[i].eps || !omega[i] || !t2_out[i] || !aligned8(omega[i]) || !aligned8(t2_out[i])) return CC_ERR_ARG;
+    k_update<<<1024, 256, 0, st>>>(sys[i].t2, omega[i], sys[i].eps, sys[i].o, sys[i].v, t2_out[i]);
+    count_launch();
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+      note_cuda(e);
+      return CC_ERR_CUDA;
+    }
+  }
+  return CC_OK;
+}
+
+int cc_ladder_status(void* ws, void* stream) {
+  if (!ws) return CC_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return CC_ERR_CUDA;
+  }
+  Status h{0, 0};
+  e = cudaMemcpy(&h, ws, sizeof(Status), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return CC_ERR_CUDA;
+  }
+  if (h.code) {
+    Status z{0, 0};
+    cudaMemcpy(ws, &z, sizeof(Status), cudaMemcpyHostToDevice);
+  }
+  return h.code;
+}
+
+int cc_ladder_debug_wait(const int* flag, long long timeout_ns, void* ws, void* stream) {
+  if (!flag || !ws || timeout_ns <= 0) return CC_ERR_ARG;
+  int rc = check_device();
+  if (rc) return rc;
+  k_debug_wait<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(flag, static_cast<unsigned long long>(timeout_ns),
+                                                                reinterpret_cast<Status*>(ws));
+  count_launch();
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return CC_ERR_CUDA;
+  }
+  return CC_OK;
+}
+
+const char* cc_ladder_strerror(int code) {
+  static thread_local std::string buf;
+  switch (code) {
+    case CC_OK: return "ok";
+    case CC_ERR_ARG: return "invalid argument (NULL pointer, dimension < 1, misalignment or size limit)";
+    case CC_ERR_DEVICE: return "current CUDA device is not sm_103 (GB300)";
+    case CC_ERR_WORKSPACE: return "workspace smaller than cc_ladder_workspace_size()";
+    case CC_ERR_TIMEOUT: return "a bounded device wait gave up (CC_ERR_TIMEOUT)";
+    case CC_ERR_CUDA: {
+      std::lock_guard<std::mutex> lk(g_err_mu);
+      buf = "CUDA error: " + g_err_text;
+      return buf.c_str();
+    }
+    default: return "unknown error code";
+  }
+}
+
+long long cc_ladder_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

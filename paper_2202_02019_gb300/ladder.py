@@ -1,0 +1,224 @@
+"""Thin ctypes binding of ``libccladder`` (see include/ccladder.h).
+
+Argument marshalling only: every step of the ladder runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams.  Importing works
+without a GPU; calling anything raises if the library or the device is
+missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+from . import _build
+
+CC_PREC = {"fp64": 0, "mixed": 1}
+CC_WS_RESIDUAL, CC_WS_DENSITY, CC_WS_LAGRANGIAN, CC_WS_STEP = 1, 2, 4, 7
+
+_lib = None
+
+
+class LadderError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class cc_ladder_system(ctypes.Structure):
+    _fields_ = [
+        ("o", ctypes.c_int32), ("v", ctypes.c_int32), ("nj", ctypes.c_int32),
+        ("L_vv", ctypes.c_void_p), ("t1", ctypes.c_void_p), ("t2", ctypes.c_void_p),
+        ("tbar2", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+    ]
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the in-tree shared library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libccladder is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, S, I, VP = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p
+    SYS = ctypes.POINTER(cc_ladder_system)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.cc_ladder_workspace_size.argtypes = [SYS, I, I, I]
+    lib.cc_ladder_workspace_size.restype = S
+    for name in ("cc_ladder_residual", "cc_ladder_density"):
+        getattr(lib, name).argtypes = [SYS, I, PP, I, VP, S, VP]
+        getattr(lib, name).restype = I
+    lib.cc_ladder_lagrangian.argtypes = [SYS, I, P, PP, I, VP, S, VP]
+    lib.cc_ladder_lagrangian.restype = I
+    lib.cc_ladder_step.argtypes = [SYS, I, PP, PP, P, I, VP, S, VP]
+    lib.cc_ladder_step.restype = I
+    lib.cc_ladder_update.argtypes = [SYS, I, PP, PP, VP]
+    lib.cc_ladder_update.restype = I
+    lib.cc_ladder_status.argtypes = [VP, VP]
+    lib.cc_ladder_status.restype = I
+    lib.cc_ladder_debug_wait.argtypes = [P, ctypes.c_longlong, VP, VP]
+    lib.cc_ladder_debug_wait.restype = I
+    lib.cc_ladder_strerror.argtypes = [I]
+    lib.cc_ladder_strerror.restype = ctypes.c_char_p
+    lib.cc_ladder_launch_count.argtypes = []
+    lib.cc_ladder_launch_count.restype = ctypes.c_longlong
+    _lib = lib
+    return lib
+
+
+EXPORTS = (
+    "cc_ladder_workspace_size", "cc_ladder_residual", "cc_ladder_density",
+    "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
+    "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
+)
+
+
+@dataclass
+class System:
+    """One closed-shell system; tensors are float64 and C-contiguous."""
+    L_vv: torch.Tensor                 # [nj, v, v]
+    t2: torch.Tensor                   # [o, o, v, v]
+    t1: Optional[torch.Tensor] = None  # [o, v]
+    tbar2: Optional[torch.Tensor] = None
+    eps: Optional[torch.Tensor] = None
+
+    @property
+    def o(self):
+        return int(self.t2.shape[0])
+
+    @property
+    def v(self):
+        return int(self.t2.shape[2])
+
+    @property
+    def nj(self):
+        return int(self.L_vv.shape[0])
+
+    def c_struct(self) -> cc_ladder_system:
+        def ptr(t):
+            if t is None:
+                return None
+            if t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("ladder tensors must be contiguous float64")
+            return t.data_ptr()
+        return cc_ladder_system(self.o, self.v, self.nj, ptr(self.L_vv), ptr(self.t1),
+                                ptr(self.t2), ptr(self.tbar2), ptr(self.eps))
+
+
+def _arr(systems: Sequence[System]):
+    arr = (cc_ladder_system * len(systems))()
+    for k, s in enumerate(systems):
+        arr[k] = s.c_struct()
+    return arr
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LadderError(rc, load().cc_ladder_strerror(rc).decode())
+
+
+def _prec(p):
+    return CC_PREC[p] if isinstance(p, str) else int(p)
+
+
+def cc_ladder_workspace_size(systems: Sequence[System], prec="mixed", which=CC_WS_STEP) -> int:
+    lib = load()
+    return int(lib.cc_ladder_workspace_size(_arr(systems), len(systems), _prec(prec), which))
+
+
+def workspace(systems: Sequence[System], prec="mixed", which=CC_WS_STEP, device=None) -> torch.Tensor:
+    n = cc_ladder_workspace_size(systems, prec, which)
+    if n == 0:
+        raise LadderError(-1, "invalid systems for workspace sizing")
+    dev = device or systems[0].L_vv.device
+    return torch.empty(n, dtype=torch.uint8, device=dev)
+
+
+def _ws(systems, prec, which, ws):
+    if ws is None:
+        ws = workspace(systems, prec, which)
+    return ws
+
+
+def cc_ladder_residual(systems, prec="mixed", ws=None, out=None, stream=None):
+    lib = load()
+    ws = _ws(systems, prec, CC_WS_RESIDUAL, ws)
+    out = out or [torch.empty_like(s.t2) for s in systems]
+    _check(lib.cc_ladder_residual(_arr(systems), len(systems), _ptrs(out), _prec(prec),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def cc_ladder_density(systems, prec="mixed", ws=None, out=None, stream=None):
+    lib = load()
+    ws = _ws(systems, prec, CC_WS_DENSITY, ws)
+    out = out or [torch.empty_like(s.L_vv) for s in systems]
+    _check(lib.cc_ladder_density(_arr(systems), len(systems), _ptrs(out), _prec(prec),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def cc_ladder_lagrangian(systems, omega=None, prec="mixed", ws=None, E=None, stream=None):
+    lib = load()
+    ws = _ws(systems, prec, CC_WS_LAGRANGIAN, ws)
+    if E is None:
+        E = torch.empty(len(systems), dtype=torch.float64, device=systems[0].L_vv.device)
+    om = _ptrs(omega) if omega is not None else None
+    _check(lib.cc_ladder_lagrangian(_arr(systems), len(systems), ctypes.c_void_p(E.data_ptr()), om,
+                                    _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                    _stream(stream)))
+    return E
+
+
+def cc_ladder_step(systems, prec="mixed", ws=None, omega=None, D=None, E=None, stream=None):
+    lib = load()
+    ws = _ws(systems, prec, CC_WS_STEP, ws)
+    omega = omega or [torch.empty_like(s.t2) for s in systems]
+    D = D or [torch.empty_like(s.L_vv) for s in systems]
+    if E is None:
+        E = torch.empty(len(systems), dtype=torch.float64, device=systems[0].L_vv.device)
+    _check(lib.cc_ladder_step(_arr(systems), len(systems), _ptrs(omega), _ptrs(D),
+                              ctypes.c_void_p(E.data_ptr()), _prec(prec),
+                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return omega, D, E
+
+
+def cc_ladder_update(systems, omega, out=None, stream=None):
+    lib = load()
+    out = out or [torch.empty_like(s.t2) for s in systems]
+    _check(lib.cc_ladder_update(_arr(systems), len(systems), _ptrs(omega), _ptrs(out), _stream(stream)))
+    return out
+
+
+def cc_ladder_status(ws, stream=None) -> int:
+    return int(load().cc_ladder_status(ctypes.c_void_p(ws.data_ptr()), _stream(stream)))
+
+
+def cc_ladder_debug_wait(flag: torch.Tensor, timeout_ns: int, ws, stream=None):
+    _check(load().cc_ladder_debug_wait(ctypes.c_void_p(flag.data_ptr()), int(timeout_ns),
+                                       ctypes.c_void_p(ws.data_ptr()), _stream(stream)))
+
+
+def cc_ladder_launch_count() -> int:
+    return int(load().cc_ladder_launch_count())
+
+
+def cc_ladder_strerror(code: int) -> str:
+    return load().cc_ladder_strerror(int(code)).decode()

@@ -1,0 +1,73 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/ccladder.h declares, sizes workspaces and rejects bad
+arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2202_02019_gb300 import ladder as lad
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "ccladder.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_ladder_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lad.load()
+    names = header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lad.EXPORTS)
+
+
+def fake_sys(o, v, nj):
+    # host-side sizing never dereferences these pointers
+    return lad.cc_ladder_system(o, v, nj, 0x1000, 0x2000, 0x3000, 0x4000, 0x5000)
+
+
+def test_workspace_size_host_only():
+    lib = lad.load()
+    for prec in (0, 1):
+        arr = (lad.cc_ladder_system * 1)(fake_sys(4, 20, 60))
+        r = lib.cc_ladder_workspace_size(arr, 1, prec, lad.CC_WS_RESIDUAL)
+        d = lib.cc_ladder_workspace_size(arr, 1, prec, lad.CC_WS_DENSITY)
+        s = lib.cc_ladder_workspace_size(arr, 1, prec, lad.CC_WS_STEP)
+        assert r > 0 and d > 0 and s >= max(r, d)
+    # retinal-scale workspace stays far below the 280 GB of one GPU
+    arr = (lad.cc_ladder_system * 1)(fake_sys(78, 650, 4000))
+    big = lib.cc_ladder_workspace_size(arr, 1, 1, lad.CC_WS_STEP)
+    assert 10e9 < big < 100e9
+    # a list is sized by its largest member
+    arr2 = (lad.cc_ladder_system * 2)(fake_sys(4, 20, 60), fake_sys(6, 30, 90))
+    one = (lad.cc_ladder_system * 1)(fake_sys(6, 30, 90))
+    assert lib.cc_ladder_workspace_size(arr2, 2, 1, 7) == lib.cc_ladder_workspace_size(one, 1, 1, 7)
+
+
+def test_host_argument_errors():
+    lib = lad.load()
+    arr = (lad.cc_ladder_system * 1)(fake_sys(0, 20, 60))
+    assert lib.cc_ladder_workspace_size(arr, 1, 1, 7) == 0
+    assert lib.cc_ladder_workspace_size(None, 1, 1, 7) == 0
+    assert lib.cc_ladder_workspace_size((lad.cc_ladder_system * 1)(fake_sys(4, 20, 60)), 1, 5, 7) == 0
+    out = (ctypes.c_void_p * 1)(0x6000)
+    assert lib.cc_ladder_residual(arr, 1, out, 1, ctypes.c_void_p(0x10000), 1 << 20, None) == -1
+    assert lib.cc_ladder_residual(None, 1, out, 1, ctypes.c_void_p(0x10000), 1 << 20, None) == -1
+    good = (lad.cc_ladder_system * 1)(fake_sys(4, 20, 60))
+    # misaligned workspace
+    assert lib.cc_ladder_residual(good, 1, out, 1, ctypes.c_void_p(0x10008), 1 << 40, None) == -1
+    # density without tbar2
+    nob = (lad.cc_ladder_system * 1)(lad.cc_ladder_system(4, 20, 60, 0x1000, 0, 0x3000, 0, 0))
+    assert lib.cc_ladder_density(nob, 1, out, 1, ctypes.c_void_p(0x10000), 1 << 40, None) == -1
+
+
+def test_strerror():
+    for code in (0, -1, -2, -3, -4, -5, -99):
+        assert isinstance(lad.cc_ladder_strerror(code), str)
+    assert "TIMEOUT" in lad.cc_ladder_strerror(-5)

@@ -1,0 +1,166 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative Frobenius error; E: relative error):
+  FP64 path   Omega, D <= 1e-11, E <= 1e-11
+  mixed path  Omega, D <= 1e-6,  E <= 1e-6
+The FP64 path only reorders FP64 sums (K-chunked DMMA, atomics), so it
+sits near 1e-15.  The mixed path carries 24-bit operands (three BF16
+pieces); the tensor core's FP32 accumulation truncates, so the leading
+piece product is re-started every 64 K terms and summed error-free, which
+leaves a small coherent bias (about -4e-8 per contraction).  E inherits
+that bias from Omega, so it is held to the same 1e-6 as Omega.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2202_02019_gb300 import ladder as lad
+from paper_2202_02019_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "mixed": 1e-6}
+TOL_E = {"fp64": 1e-11, "mixed": 1e-6}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev_sys(s, tb2, L=None):
+    d = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(d)
+    return lad.System(L_vv=t(s.L_vv if L is None else L), t2=t(s.t2), t1=t(s.t1), tbar2=t(tb2), eps=t(s.eps))
+
+
+CASES = {
+    "tiny_4_20_60": (4, 20, 60, 12.0),
+    "odd_3_7_5": (3, 7, 5, 4.0),
+    "o1_1_9_7": (1, 9, 7, 4.0),
+    "v1_3_1_5": (3, 1, 5, 4.0),
+    "v2_2_2_3": (2, 2, 3, 4.0),
+    "ragged_5_37_70": (5, 37, 70, 20.0),
+    "fd_8_48_160": (8, 48, 160, 160 / 6.0),
+}
+
+_cache = {}
+
+
+def ref(name):
+    if name not in _cache:
+        o, v, nj, lam = CASES[name]
+        s, tb1, tb2 = synth.make_pair(o, v, nj, lam, seed=2202)
+        tt = O.tau(s.t1, s.t2)
+        om = O.residual_rows(s.L_vv, tt)
+        D = O.density_rows(s.L_vv, tb2, tt)
+        _cache[name] = (s, tb2, om, D, O.lagrangian(tb2, om))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_matches_oracle(name, prec):
+    s, tb2, om_ref, D_ref, E_ref = ref(name)
+    sd = dev_sys(s, tb2)
+    ws = lad.workspace([sd], prec)
+    om, D, E = lad.cc_ladder_step([sd], prec=prec, ws=ws)
+    assert lad.cc_ladder_status(ws) == 0
+    eo, ed = rel(om[0].cpu(), om_ref), rel(D[0].cpu(), D_ref)
+    ee = abs(float(E[0]) - E_ref) / abs(E_ref)
+    print(f"{name} {prec}: Omega {eo:.2e} D {ed:.2e} E {ee:.2e}")
+    assert eo < TOL[prec] and ed < TOL[prec] and ee < TOL_E[prec], (eo, ed, ee)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_separate_entry_points(prec):
+    s, tb2, om_ref, D_ref, E_ref = ref("ragged_5_37_70")
+    sd = dev_sys(s, tb2)
+    om = lad.cc_ladder_residual([sd], prec=prec)
+    D = lad.cc_ladder_density([sd], prec=prec)
+    E1 = lad.cc_ladder_lagrangian([sd], omega=om, prec=prec)
+    E2 = lad.cc_ladder_lagrangian([sd], omega=None, prec=prec)
+    torch.cuda.synchronize()
+    assert rel(om[0].cpu(), om_ref) < TOL[prec]
+    assert rel(D[0].cpu(), D_ref) < TOL[prec]
+    for E in (E1, E2):
+        assert abs(float(E[0]) - E_ref) < TOL_E[prec] * abs(E_ref)
+    # plain FP64 reduction of the same Omega: identical up to summation order
+    assert abs(float(E1[0]) - float(E2[0])) < 1e-12 * abs(E_ref) + (0 if prec == "fp64" else 1e-9 * abs(E_ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_nonsymmetric_L(prec):
+    """Kernels do not assume L^J_ac = L^J_ca."""
+    s, tb1, tb2 = synth.make_pair(3, 11, 9, 6.0, seed=99)
+    rng = np.random.default_rng(5)
+    L = s.L_vv + 0.3 * rng.standard_normal(s.L_vv.shape)
+    tt = O.tau(s.t1, s.t2)
+    om_ref = O.residual_dense(L, tt)
+    D_ref = O.density_dense(L, tb2, tt)
+    om, D, E = lad.cc_ladder_step([dev_sys(s, tb2, L)], prec=prec)
+    torch.cuda.synchronize()
+    assert rel(om[0].cpu(), om_ref) < TOL[prec]
+    assert rel(D[0].cpu(), D_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_t1_none(prec):
+    s, tb2, _, _, _ = ref("odd_3_7_5")
+    sd = dev_sys(s, tb2)
+    sd.t1 = None
+    om = lad.cc_ladder_residual([sd], prec=prec)
+    torch.cuda.synchronize()
+    assert rel(om[0].cpu(), O.residual_dense(s.L_vv, s.t2)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_single(prec):
+    names = ["odd_3_7_5", "tiny_4_20_60", "ragged_5_37_70"]
+    systems = [dev_sys(*ref(n)[:2]) for n in names]
+    om_b, D_b, E_b = lad.cc_ladder_step(systems, prec=prec)
+    for k, sd in enumerate(systems):
+        om1, D1, E1 = lad.cc_ladder_step([sd], prec=prec)
+        torch.cuda.synchronize()
+        # same kernels, same tiles, same summation order: bit-for-bit
+        assert torch.equal(om_b[k], om1[0]) or prec == "mixed" and rel(om_b[k].cpu(), om1[0].cpu()) < 1e-12
+        assert rel(D_b[k].cpu(), D1[0].cpu()) < (1e-15 if prec == "fp64" else 1e-12)
+        assert rel(om_b[k].cpu(), ref(names[k])[2]) < TOL[prec]
+
+
+def test_update_matches_oracle():
+    s, tb2, om_ref, _, _ = ref("tiny_4_20_60")
+    sd = dev_sys(s, tb2)
+    om = lad.cc_ladder_residual([sd], prec="fp64")
+    t_new = lad.cc_ladder_update([sd], om)
+    torch.cuda.synchronize()
+    expect = O.update_t2(s.t2, om[0].cpu().numpy(), s.eps, s.o)
+    assert rel(t_new[0].cpu(), expect) < 1e-15
+
+
+def test_workspace_too_small_is_rejected():
+    s, tb2, _, _, _ = ref("odd_3_7_5")
+    sd = dev_sys(s, tb2)
+    n = lad.cc_ladder_workspace_size([sd], "mixed", lad.CC_WS_STEP)
+    ws = torch.empty(n - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lad.LadderError) as e:
+        lad.cc_ladder_step([sd], prec="mixed", ws=ws)
+    assert e.value.code == -3
+
+
+def test_bounded_wait_times_out_and_recovers():
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lad.cc_ladder_debug_wait(flag, 20_000_000, ws)          # nothing ever sets it
+    assert lad.cc_ladder_status(ws) == -5
+    assert lad.cc_ladder_status(ws) == 0                    # status is cleared once read
+    flag.fill_(1)
+    lad.cc_ladder_debug_wait(flag, 20_000_000, ws)
+    assert lad.cc_ladder_status(ws) == 0
+    # the context is still usable afterwards
+    s, tb2, om_ref, _, _ = ref("odd_3_7_5")
+    om = lad.cc_ladder_residual([dev_sys(s, tb2)], prec="mixed")
+    torch.cuda.synchronize()
+    assert rel(om[0].cpu(), om_ref) < TOL["mixed"]
