@@ -1,0 +1,380 @@
+"""Benchmark of the CD-CCSD vvvv ladder hot path (Omega + D^J + E) on GB300.
+
+One step = one cc_ladder_step call: the ladder residual Omega, the
+three-index density D^J and the Lagrangian E of one retinal-scale system
+(o=78, v=650, N_J=4000) in the mixed (split-BF16 tensor-core) path, with
+inputs already resident in HBM.  The metric is useful TFLOP/s, counted with
+the packed (+-) algorithm's flop formula
+
+    F = 2 P+ v^2 N_J + 4 (P+^2 Q+ + P-^2 Q-) + 2 v^4 N_J,
+    P+- = v(v+-1)/2, Q+- = o(o+-1)/2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own system (weak scaling, no collective on
+the data path); value = N * F / (max over ranks of the step time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (o, v, nj, lam_scale)
+    "retinal": (78, 650, 4000, 700.0),
+    "small": (24, 180, 900, 150.0),
+    "grad": (30, 250, 1200, 200.0),
+}
+METRIC = "ladder Omega + D^J useful TFLOP/s (mixed split-BF16 path), o78/v650/NJ4000"
+
+
+def counted_flops(o, v, nj):
+    pvp, pvm = v * (v + 1) // 2, v * (v - 1) // 2
+    qop, qom = o * (o + 1) // 2, o * (o - 1) // 2
+    return 2.0 * pvp * v * v * nj + 4.0 * (pvp * pvp * qop + pvm * pvm * qom) + 2.0 * float(v) ** 4 * nj
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return {"bf16": float(d.get("bf16_tflops")), "bf16_sustained": float(d.get("bf16_tflops_sustained")),
+                    "hbm": float(d.get("hbm_gbs")), "source": "measured"}
+        except Exception:
+            pass
+    return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "power_w_median": statistics.median(pw) if pw else None,
+                "samples": len(rows)}
+
+
+def host_cores():
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count()
+    return n
+
+
+# ---------------------------------------------------------------------------
+# oracle leg (CPU): bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(h, rows, cols):
+    """Time the FP64 oracle on Omega[:, :, a, cols] and D[:, a, cols] for a in rows."""
+    import oracle as O
+    t0 = time.perf_counter()
+    tt = O.tau(h["t1"], h["t2"])
+    om = O.residual_rows(h["L_vv"], tt, rows, cols)
+    D = O.density_rows(h["L_vv"], h["tbar2"], tt, rows, cols)
+    return time.perf_counter() - t0, om, D
+
+
+def sample_spec(v, n_rows=2, n_cols=64):
+    rows = [int(round(k * (v - 1) / max(1, n_rows - 1))) for k in range(n_rows)] if n_rows > 1 else [v // 2]
+    step = max(1, v // n_cols)
+    cols = list(range(0, v, step))[:n_cols]
+    return rows, cols
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    from paper_2202_02019_gb300 import synth
+    o, v, nj, lam = WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    d = synth.make_pair_torch(o, v, nj, lam, seed=2202, device=dev)
+    h = {k: d[k].cpu().numpy() for k in ("L_vv", "t1", "t2", "tbar2")}
+    del d
+    rows, cols = sample_spec(v)
+    F = counted_flops(o, v, nj)
+    frac = len(rows) * len(cols) / float(v * v)
+    for _ in range(args.warmup):
+        oracle_sample(h, rows[:1], cols[:8])
+    times = []
+    for _ in range(args.steps):
+        t, _, _ = oracle_sample(h, rows, cols)
+        times.append(t)
+    t = statistics.mean(times)
+    val = F * frac / t / 1e12
+    cores = host_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "sample": f"rows {rows} x cols {len(cols)}"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"Omega[:,:,a,b] and D[:,a,c] for a in {rows}, {len(cols)} b/c columns "
+                                   f"({frac:.2e} of the outputs), credited F*{frac:.2e}"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def rel(a, b):
+    import numpy as np
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def fp64_vs_mixed_small(lad, synth, torch):
+    """Both paths on the small single-system config (o=24, v=180, N_J=900)."""
+    import numpy as np
+    import oracle as O
+    o, v, nj, lam = WORKLOADS["small"]
+    s, tb1, tb2 = synth.make_pair(o, v, nj, lam, seed=2202)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sd = lad.System(L_vv=t(s.L_vv), t2=t(s.t2), t1=t(s.t1), tbar2=t(tb2), eps=t(s.eps))
+    res = {"workload": f"small o={o} v={v} nj={nj}"}
+    rows, cols = [0, v // 2, v - 1], list(range(0, v, 6))
+    tt = O.tau(s.t1, s.t2)
+    om_ref = O.residual_rows(s.L_vv, tt, rows)
+    D_ref = O.density_rows(s.L_vv, tb2, tt, rows)
+    F = counted_flops(o, v, nj)
+    outs = {}
+    for prec in ("mixed", "fp64"):
+        ws = lad.workspace([sd], prec)
+        om, D, E = lad.cc_ladder_step([sd], prec=prec, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        om, D, E = lad.cc_ladder_step([sd], prec=prec, ws=ws, omega=om, D=D, E=E)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        outs[prec] = (om[0], D[0], float(E[0]))
+        res[prec] = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12,
+                     "rel_err_omega_vs_oracle_rows": rel(om[0][:, :, rows, :].cpu(), om_ref),
+                     "rel_err_D_vs_oracle_rows": rel(D[0][:, rows, :].cpu(), D_ref)}
+        del ws
+    om64, D64, E64 = outs["fp64"]
+    omm, Dm, Em = outs["mixed"]
+    res["mixed_vs_fp64"] = {"rel_err_omega": rel(omm.cpu(), om64.cpu()), "rel_err_D": rel(Dm.cpu(), D64.cpu()),
+                            "rel_err_E": abs(Em - E64) / abs(E64)}
+    res["speedup_mixed_over_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    return res
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2202_02019_gb300 import ladder as lad
+    from paper_2202_02019_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lad.load()
+    o, v, nj, lam = WORKLOADS[args.workload]
+    F = counted_flops(o, v, nj)
+    d = synth.make_pair_torch(o, v, nj, lam, seed=2202 + 17 * rank, device="cuda")
+    sd = lad.System(L_vv=d["L_vv"], t2=d["t2"], t1=d["t1"], tbar2=d["tbar2"], eps=d["eps"])
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    ws = lad.workspace([sd], "mixed")
+    om = [torch.empty_like(sd.t2)]
+    D = [torch.empty_like(sd.L_vv)]
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lad.cc_ladder_step([sd], prec="mixed", ws=ws, omega=om, D=D, E=E, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    assert lad.cc_ladder_status(ws) == 0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    lad.cc_ladder_profile(True)
+    n0 = lad.cc_ladder_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = lad.cc_ladder_launch_count() - n0
+    gemm_ms, gemm_n, gemm_fl = lad.cc_ladder_profile_read()
+    lad.cc_ladder_profile(False)
+    status = lad.cc_ladder_status(ws)
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t[0])
+    value = world * F / (ms_max * 1e-3) / 1e12
+
+    pk = peaks()
+    gemm_ms_step = gemm_ms / args.steps
+    achieved = F / (gemm_ms_step * 1e-3) / 1e12
+    peak_useful = pk["bf16_sustained"] / 6.0
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_useful, "unit": "TFLOP/s",
+                "frac": achieved / peak_useful, "traffic": None,
+                "kernel": "cc_gemm_split3_tc", "peak_basis": f"{pk['source']} sustained BF16 / 6 products",
+                "kernel_share_of_step": gemm_ms_step / ms,
+                "kernel_launches_per_step": gemm_n / args.steps,
+                "padded_flops_per_step": gemm_fl / args.steps}
+
+    extra = {}
+    cpu = None
+    e2e = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        # end to end through the C ABI with host buffers (pinned)
+        host = {k: torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for k, x in
+                (("L_vv", sd.L_vv), ("t1", sd.t1), ("t2", sd.t2), ("tbar2", sd.tbar2), ("eps", sd.eps))}
+        for k in host:
+            host[k].copy_(getattr(sd, k))
+        h_om = torch.empty(sd.t2.shape, dtype=torch.float64, pin_memory=True)
+        h_D = torch.empty(sd.L_vv.shape, dtype=torch.float64, pin_memory=True)
+        h_E = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        # parity on a bounded sample against the oracle (uses the timed step's outputs)
+        rows, cols = sample_spec(v)
+        g_om = om[0][:, :, rows, :][:, :, :, cols].cpu().numpy()
+        g_D = D[0][:, rows, :][:, :, cols].cpu().numpy()
+        g_E = float(E[0])
+        hn = {k: host[k].numpy() for k in ("L_vv", "t1", "t2", "tbar2")}
+        t_or, o_om, o_D = oracle_sample(hn, rows, cols)
+        frac = len(rows) * len(cols) / float(v * v)
+        cpu = {"value": F * frac / t_or / 1e12, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"Omega[:,:,a,b] and D[:,a,c] for a in {rows}, {len(cols)} b/c columns "
+                         f"({frac:.2e} of the outputs, credited F*{frac:.2e}); {t_or:.1f} s"}
+        extra["parity_sampled"] = {"rel_err_omega": rel(g_om, o_om), "rel_err_D": rel(g_D, o_D),
+                                   "rows": rows, "n_cols": len(cols)}
+        # Euler identity check on the full outputs: sum L.D = E
+        eul = float(torch.sum(sd.L_vv * D[0]))
+        extra["euler_identity_rel"] = abs(eul - g_E) / abs(g_E)
+        del hn
+        # e2e: H2D inputs, step, D2H outputs, all inside the timed region
+        dev_in = {k: torch.empty_like(getattr(sd, k)) for k in host}
+        sd2 = lad.System(**dev_in)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in host:
+            dev_in[k].copy_(host[k], non_blocking=True)
+        lad.cc_ladder_step([sd2], prec="mixed", ws=ws, omega=om, D=D, E=E, stream=stream)
+        h_om.copy_(om[0], non_blocking=True)
+        h_D.copy_(D[0], non_blocking=True)
+        h_E.copy_(E, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        h2d = sum(x.numel() * x.element_size() for x in host.values())
+        d2h = h_om.numel() * 8 + h_D.numel() * 8 + 8
+        e2e = {"value": F / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms": e2e_ms}
+        del host, h_om, h_D, dev_in, sd2
+        extra["E"] = g_E
+        if not args.no_small:
+            del ws
+            torch.cuda.empty_cache()
+            extra["small_config_fp64_vs_mixed"] = fp64_vs_mixed_small(lad, synth, torch)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3 split (FP32 accumulate, FP64 reductions)",
+            "data": "synthetic (seeded, device generator; recipe in DESIGN.md)",
+            "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "global_batch": world,
+                       "parallelism": f"independent systems, one per GPU ({world})",
+                       "l2": "inputs larger than L2 (55 GB resident), no flush needed",
+                       "counted_flops_per_system": F},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "device_status": status,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="retinal", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, oracle sample and small-config legs")
+    ap.add_argument("--no-small", action="store_true", help="skip the small-config FP64-vs-mixed leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -143,6 +143,15 @@ const char* cc_ladder_strerror(int code);
  * (a host-side counter). */
 long long cc_ladder_launch_count(void);
 
+/* Instrumentation (not part of the paper's method).  cc_ladder_profile(1)
+ * makes every later call record a CUDA event pair on its stream around each
+ * tensor-core contraction launch; cc_ladder_profile_read() waits for the
+ * recorded events and returns the summed contraction time in milliseconds,
+ * the number of contraction launches and their padded 2*M*N*K flop count,
+ * then clears them.  cc_ladder_profile(0) switches recording off. */
+void cc_ladder_profile(int enable);
+int cc_ladder_profile_read(double* gemm_ms, long long* gemm_launches, double* gemm_flops);
+
 #ifdef __cplusplus
 }
 #endif

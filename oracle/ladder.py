@@ -93,8 +93,8 @@ def dE_dtau(L_vv, tbar2):
 # --------------------------------------------------------------------------
 # row-blocked formulation: one virtual row a at a time, no V^4 array
 # --------------------------------------------------------------------------
-def residual_rows(L_vv, tau_, rows=None):
-    """Omega[:, :, a, :] for a in ``rows`` (all rows if None).
+def residual_rows(L_vv, tau_, rows=None, cols=None):
+    """Omega[:, :, a, b] for a in ``rows`` and b in ``cols`` (all if None).
 
     For a fixed a:  G^a[c, (b,d)] = sum_J L^J_ac L^J_bd  (a v x v^2 block of
     g, never the whole V^4), then Omega_ij^ab = sum_{c,d} G^a[c,b,d] tau_ij^cd.
@@ -102,18 +102,20 @@ def residual_rows(L_vv, tau_, rows=None):
     nj, v, _ = L_vv.shape
     o = tau_.shape[0]
     rows = range(v) if rows is None else rows
-    Lf = L_vv.reshape(nj, v * v)
+    cols = np.arange(v) if cols is None else np.asarray(cols)
+    nb = len(cols)
+    Lb = L_vv[:, cols, :].reshape(nj, nb * v)
     T = tau_.reshape(o * o, v * v)
-    out = np.empty((o, o, len(rows), v))
+    out = np.empty((o, o, len(rows), nb))
     for k, a in enumerate(rows):
-        Ga = (L_vv[:, a, :].T @ Lf).reshape(v, v, v)          # [c, b, d]
-        Gb = Ga.transpose(1, 0, 2).reshape(v, v * v)           # [b, (c,d)]
-        out[:, :, k, :] = (Gb @ T.T).T.reshape(o, o, v)
+        Ga = (L_vv[:, a, :].T @ Lb).reshape(v, nb, v)         # [c, b, d]
+        Gb = Ga.transpose(1, 0, 2).reshape(nb, v * v)          # [b, (c,d)]
+        out[:, :, k, :] = (Gb @ T.T).T.reshape(o, o, nb)
     return out
 
 
-def density_rows(L_vv, tbar2, tau_, rows=None):
-    """D[:, a, :] for a in ``rows``.
+def density_rows(L_vv, tbar2, tau_, rows=None, cols=None):
+    """D[:, a, c] for a in ``rows`` and c in ``cols`` (all if None).
 
     For a fixed a:  Gamma^a[b, (c,d)] = sum_ij tbar_ij^ab tau_ij^cd, then
     D^J_ac = sum_{b,d} Gamma^a[b,c,d] L^J_bd.
@@ -121,21 +123,23 @@ def density_rows(L_vv, tbar2, tau_, rows=None):
     nj, v, _ = L_vv.shape
     o = tau_.shape[0]
     rows = range(v) if rows is None else rows
+    cols = np.arange(v) if cols is None else np.asarray(cols)
+    nc = len(cols)
     Lf = L_vv.reshape(nj, v * v)
-    T = tau_.reshape(o * o, v * v)
-    out = np.empty((nj, len(rows), v))
+    Tc = tau_[:, :, cols, :].reshape(o * o, nc * v)
+    out = np.empty((nj, len(rows), nc))
     for k, a in enumerate(rows):
         Ta = tbar2[:, :, a, :].reshape(o * o, v)              # [(ij), b]
-        Ga = (Ta.T @ T).reshape(v, v, v)                       # [b, c, d]
-        Gc = Ga.transpose(1, 0, 2).reshape(v, v * v)           # [c, (b,d)]
+        Ga = (Ta.T @ Tc).reshape(v, nc, v)                     # [b, c, d]
+        Gc = Ga.transpose(1, 0, 2).reshape(nc, v * v)          # [c, (b,d)]
         out[:, k, :] = (Gc @ Lf.T).T
     return out
 
 
-def sampled_rows(L_vv, t1, t2, tbar2, rows):
-    """(Omega[:, :, rows, :], D[:, rows, :]) for a list of virtual rows."""
+def sampled_rows(L_vv, t1, t2, tbar2, rows, cols=None):
+    """(Omega[:, :, rows, cols], D[:, rows, cols]) for lists of virtual indices."""
     tt = tau(t1, t2)
-    return residual_rows(L_vv, tt, rows), density_rows(L_vv, tbar2, tt, rows)
+    return residual_rows(L_vv, tt, rows, cols), density_rows(L_vv, tbar2, tt, rows, cols)
 
 
 # --------------------------------------------------------------------------

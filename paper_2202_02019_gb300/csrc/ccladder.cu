@@ -505,17 +505,65 @@ struct Ctx {
   }
 };
 
+// Optional instrumentation: CUDA events recorded on the launching stream
+// around every contraction launch, summed when read.
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  size_t used = 0;
+  double flops = 0.0;
+  long long launches = 0;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+static Profiler g_prof;
+
+template <typename F>
+static int profiled(const GemmOp& g, cudaStream_t s, F&& launch) {
+  bool on;
+  {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    on = g_prof.on;
+  }
+  if (!on) return launch();
+  cudaEvent_t e0, e1;
+  {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    e0 = g_prof.get();
+    e1 = g_prof.get();
+    g_prof.pending.emplace_back(e0, e1);
+    g_prof.flops += 2.0 * static_cast<double>(g.M) * static_cast<double>(g.N) * static_cast<double>(g.K);
+    g_prof.launches += 1;
+  }
+  cudaEventRecord(e0, s);
+  const int rc = launch();
+  cudaEventRecord(e1, s);
+  return rc;
+}
+
 template <typename T>
 struct Path;
 template <>
 struct Path<double> {
   static constexpr int NP = 1;
-  static int gemm(const GemmOp& g, cudaStream_t s) { return gemm_f64(g, s); }
+  static int gemm(const GemmOp& g, cudaStream_t s) {
+    return profiled(g, s, [&] { return gemm_f64(g, s); });
+  }
 };
 template <>
 struct Path<__nv_bfloat16> {
   static constexpr int NP = 3;
-  static int gemm(const GemmOp& g, cudaStream_t s) { return gemm_mixed(g, s); }
+  static int gemm(const GemmOp& g, cudaStream_t s) {
+    return profiled(g, s, [&] { return gemm_mixed(g, s); });
+  }
 };
 
 template <typename T>
@@ -917,5 +965,33 @@ const char* cc_ladder_strerror(int code) {
 }
 
 long long cc_ladder_launch_count(void) { return g_launches.load(); }
+
+void cc_ladder_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = enable != 0;
+  g_prof.pending.clear();
+  g_prof.used = 0;
+  g_prof.flops = 0.0;
+  g_prof.launches = 0;
+}
+
+int cc_ladder_profile_read(double* gemm_ms, long long* gemm_launches, double* gemm_flops) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  double ms = 0.0;
+  for (auto& pr : g_prof.pending) {
+    if (cudaEventSynchronize(pr.second) != cudaSuccess) return CC_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess) return CC_ERR_CUDA;
+    ms += t;
+  }
+  if (gemm_ms) *gemm_ms = ms;
+  if (gemm_launches) *gemm_launches = g_prof.launches;
+  if (gemm_flops) *gemm_flops = g_prof.flops;
+  g_prof.pending.clear();
+  g_prof.used = 0;
+  g_prof.flops = 0.0;
+  g_prof.launches = 0;
+  return CC_OK;
+}
 
 }  // extern "C"

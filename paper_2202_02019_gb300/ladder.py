@@ -69,6 +69,11 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_strerror.restype = ctypes.c_char_p
     lib.cc_ladder_launch_count.argtypes = []
     lib.cc_ladder_launch_count.restype = ctypes.c_longlong
+    lib.cc_ladder_profile.argtypes = [I]
+    lib.cc_ladder_profile.restype = None
+    lib.cc_ladder_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_double)]
+    lib.cc_ladder_profile_read.restype = I
     _lib = lib
     return lib
 
@@ -77,6 +82,7 @@ EXPORTS = (
     "cc_ladder_workspace_size", "cc_ladder_residual", "cc_ladder_density",
     "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
+    "cc_ladder_profile", "cc_ladder_profile_read",
 )
 
 
@@ -222,3 +228,14 @@ def cc_ladder_launch_count() -> int:
 
 def cc_ladder_strerror(code: int) -> str:
     return load().cc_ladder_strerror(int(code)).decode()
+
+
+def cc_ladder_profile(enable: bool):
+    load().cc_ladder_profile(1 if enable else 0)
+
+
+def cc_ladder_profile_read():
+    """(contraction ms, contraction launches, padded contraction flops) since the last read."""
+    ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+    _check(load().cc_ladder_profile_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
+    return ms.value, n.value, fl.value

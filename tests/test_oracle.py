@@ -118,6 +118,10 @@ def test_rows_subset(tiny):
     D_d = O.density_dense(s.L_vv, tb, tt)
     assert rel(om, om_d[:, :, rows, :]) < 1e-13
     assert rel(D, D_d[:, rows, :]) < 1e-13
+    cols = [3, 4, 11, 18]
+    om2, D2 = O.sampled_rows(s.L_vv, s.t1, s.t2, tb, rows, cols)
+    assert rel(om2, om_d[:, :, rows, :][:, :, :, cols]) < 1e-13
+    assert rel(D2, D_d[:, rows, :][:, :, cols]) < 1e-13
 
 
 # ------------------------------------------------------------------ symmetries
