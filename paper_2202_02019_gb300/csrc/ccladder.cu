@@ -184,13 +184,17 @@ __device__ __forceinline__ void tile_pair(int idx, int nt, int& ct, int& dt) {
   dt = static_cast<int>(idx - pair_sym(r, r, nt)) + r;
 }
 
-// G (FP64, rows (b_l,d), columns (a_l,c), pitch ldG) -> g^pm packed rows
-template <typename T>
-__global__ void k_pack_g(const double* __restrict__ G, int64_t ldG, int v, int a0, int b0, int nb, int diag, int nt,
+// G (rows (b_l,d), columns (a_l,c), pitch ldG; FP64 or float-float) ->
+// g^pm packed rows:  g+[ab][k+(c,d)] = G_cd + G_dc (G_cc on the diagonal),
+//                    g-[ab][k-(c,d)] = G_cd - G_dc (0 for a = b).
+template <typename T, typename S>
+__global__ void k_pack_g(const S* __restrict__ G, int64_t ldG, int v, int a0, int b0, int nb, int diag, int nt,
                          T* __restrict__ gp, int64_t ldp, int64_t ppiece, T* __restrict__ gm, int64_t ldm,
                          int64_t mpiece, int minus) {
-  __shared__ double s1[32][33];  // s1[dd][cc] = G^{ab}_{c,d}
-  __shared__ double s2[32][33];  // s2[cc][dd] = G^{ab}_{d,c}
+  using A = Ar<S>;
+  using V = typename A::V;
+  __shared__ V s1[32][33];  // s1[dd][cc] = G^{ab}_{c,d}
+  __shared__ V s2[32][33];  // s2[cc][dd] = G^{ab}_{d,c}
   const int64_t pr = blockIdx.y;
   int al, bl;
   pb_pair(pr, nb, diag, al, bl);
@@ -202,18 +206,19 @@ __global__ void k_pack_g(const double* __restrict__ G, int64_t ldG, int v, int a
   const int64_t rowB = static_cast<int64_t>(bl) * v;
   for (int r = ty; r < 32; r += 8) {
     const int d = d0 + r, c = c0 + tx;
-    s1[r][tx] = (c < v && d < v) ? G[(rowB + d) * ldG + colA + c] : 0.0;
+    s1[r][tx] = (c < v && d < v) ? A::ld(G, (rowB + d) * ldG + colA + c) : A::zero();
     const int c2 = c0 + r, d2 = d0 + tx;
-    s2[r][tx] = (c2 < v && d2 < v) ? G[(rowB + c2) * ldG + colA + d2] : 0.0;
+    s2[r][tx] = (c2 < v && d2 < v) ? A::ld(G, (rowB + c2) * ldG + colA + d2) : A::zero();
   }
   __syncthreads();
   const bool same = (a0 + al) == (b0 + bl);
   for (int r = ty; r < 32; r += 8) {
     const int c = c0 + r, d = d0 + tx;
     if (c >= v || d >= v || d < c) continue;
-    const double gcd = s1[tx][r], gdc = s2[r][tx];
-    Store<T>::put(gp, pr * ldp + pair_sym(c, d, v), ppiece, (c == d) ? gcd : gcd + gdc);
-    if (minus && c < d) Store<T>::put(gm, pr * ldm + pair_strict(c, d, v), mpiece, same ? 0.0 : gcd - gdc);
+    const V gcd = s1[tx][r], gdc = s2[r][tx];
+    Put<T, V>::put(gp, pr * ldp + pair_sym(c, d, v), ppiece, (c == d) ? gcd : A::add(gcd, gdc));
+    if (minus && c < d)
+      Put<T, V>::put(gm, pr * ldm + pair_strict(c, d, v), mpiece, same ? A::zero() : A::sub(gcd, gdc));
   }
 }
 
@@ -234,24 +239,28 @@ __device__ __forceinline__ double block_sum(double x) {
 }
 
 // Omega^pm [occupied pair][local pair] -> Omega_ij^ab (and/or the E partial)
-__global__ void k_unpack_omega(const double* __restrict__ Op, const double* __restrict__ Om, int64_t ldO, int o,
-                               int v, int a0, int b0, int nb, int diag, int64_t npairs, int minus,
+template <typename S>
+__global__ void k_unpack_omega(const S* __restrict__ Op, const S* __restrict__ Om, int64_t ldO, int o, int v,
+                               int a0, int b0, int nb, int diag, int64_t npairs, int minus,
                                double* __restrict__ omega, const double* __restrict__ tbar2,
                                double* __restrict__ epart) {
+  using A = Ar<S>;
+  using V = typename A::V;
   const int i = blockIdx.x / o, j = blockIdx.x % o;
   const int lo = min(i, j), hi = max(i, j);
   const int64_t pp = pair_sym(lo, hi, o);
   const int64_t pm = (i != j) ? pair_strict(lo, hi, o) : -1;
-  const double sg = (i < j) ? 1.0 : -1.0;
+  const bool neg = i > j;
   const int64_t base = (static_cast<int64_t>(i) * o + j) * v * v;
   double esum = 0.0;
   for (int64_t pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
     int al, bl;
     pb_pair(pr, nb, diag, al, bl);
     const int a = a0 + al, b = b0 + bl;
-    const double P = Op[pp * ldO + pr];
-    const double M = (minus && pm >= 0) ? sg * Om[pm * ldO + pr] : 0.0;
-    const double wab = 0.5 * (P + M), wba = 0.5 * (P - M);
+    const V P = A::ld(Op, pp * ldO + pr);
+    V M = (minus && pm >= 0) ? A::ld(Om, pm * ldO + pr) : A::zero();
+    if (neg) M = A::sub(A::zero(), M);
+    const double wab = 0.5 * A::to_d(A::add(P, M)), wba = 0.5 * A::to_d(A::sub(P, M));
     const int64_t iab = base + static_cast<int64_t>(a) * v + b, iba = base + static_cast<int64_t>(b) * v + a;
     if (omega) {
       omega[iab] = wab;
@@ -263,8 +272,8 @@ __global__ void k_unpack_omega(const double* __restrict__ Op, const double* __re
     }
   }
   if (epart) {
-    const double s = block_sum(esum);
-    if (threadIdx.x == 0) epart[blockIdx.x] = s;
+    const double sm = block_sum(esum);
+    if (threadIdx.x == 0) epart[blockIdx.x] = sm;
   }
 }
 
@@ -273,12 +282,14 @@ __global__ void k_unpack_omega(const double* __restrict__ Op, const double* __re
 //   bot[(x_l v + c)][(y_l vp + d)]  x in block beta,  y in block alpha
 // Gamma_abcd = P(cd) + sgn(c,d) M(cd) for the stored pair (a<=b),
 // Gamma_bacd = P(cd) - sgn(c,d) M(cd); P symmetric, M antisymmetric in cd.
-template <typename T>
-__global__ void k_unpack_gamma(const double* __restrict__ Gp, const double* __restrict__ Gm, int64_t ldp,
-                               int64_t ldm, int v, int vp, int a0, int b0, int nb, int diag, int nt, int minus,
+template <typename T, typename S>
+__global__ void k_unpack_gamma(const S* __restrict__ Gp, const S* __restrict__ Gm, int64_t ldp, int64_t ldm,
+                               int v, int vp, int a0, int b0, int nb, int diag, int nt, int minus,
                                T* __restrict__ top, int64_t ldt, int64_t tpiece, T* __restrict__ bot, int64_t ldb,
                                int64_t bpiece) {
-  __shared__ double sP[32][33], sM[32][33];  // [c - c0][d - d0], c <= d
+  using A = Ar<S>;
+  using V = typename A::V;
+  __shared__ V sP[32][33], sM[32][33];  // [c - c0][d - d0], c <= d
   const int64_t pr = blockIdx.y;
   int al, bl;
   pb_pair(pr, nb, diag, al, bl);
@@ -289,15 +300,14 @@ __global__ void k_unpack_gamma(const double* __restrict__ Gp, const double* __re
   for (int r = ty; r < 32; r += 8) {
     const int c = c0 + r, d = d0 + tx;
     const bool in = c < v && d < v && c <= d;
-    sP[r][tx] = in ? Gp[pr * ldp + pair_sym(c, d, v)] : 0.0;
-    sM[r][tx] = (in && minus && c < d) ? Gm[pr * ldm + pair_strict(c, d, v)] : 0.0;
+    sP[r][tx] = in ? A::ld(Gp, pr * ldp + pair_sym(c, d, v)) : A::zero();
+    sM[r][tx] = (in && minus && c < d) ? A::ld(Gm, pr * ldm + pair_strict(c, d, v)) : A::zero();
   }
   __syncthreads();
   const bool same = (a0 + al) == (b0 + bl);
-  // ordered pairs (x, y): (a, b) with sign +1, (b, a) with sign -1
+  // ordered pairs (x, y): (a, b) adds sgn M, (b, a) subtracts it
   for (int which = 0; which < 2; ++which) {
     if (which == 1 && same) break;
-    const double sp = which == 0 ? 1.0 : -1.0;
     T* dst;
     int64_t ld, piece, xrow, ycol;
     if (which == 0) {
@@ -317,12 +327,23 @@ __global__ void k_unpack_gamma(const double* __restrict__ Gp, const double* __re
         const int row = R0 + r, col = W0 + tx;
         if (row >= v || col >= v) continue;
         const int lo = min(row, col), hi = max(row, col);
-        const double P = sP[lo - c0][hi - d0];
-        const double M = sM[lo - c0][hi - d0];
-        const double sgn = row < col ? 1.0 : (row > col ? -1.0 : 0.0);
-        Store<T>::put(dst, (xrow + row) * ld + ycol + col, piece, P + sp * sgn * M);
+        const V P = sP[lo - c0][hi - d0];
+        const V M = sM[lo - c0][hi - d0];
+        // sign of M: +1 above the diagonal for (a, b), flipped below it and for (b, a)
+        const bool addM = (row < col) == (which == 0);
+        const V val = (row == col) ? P : (addM ? A::add(P, M) : A::sub(P, M));
+        Put<T, V>::put(dst, (xrow + row) * ld + ycol + col, piece, val);
       }
     }
+  }
+}
+
+// float-float -> FP64 (the final three-index density)
+__global__ void k_ff_to_f64(const float2* __restrict__ in, double* __restrict__ out, int64_t n) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float2 x = in[k];
+    out[k] = static_cast<double>(x.x) + static_cast<double>(x.y);
   }
 }
 
@@ -388,11 +409,11 @@ struct Plan {
   int64_t Kj = 0, Kvp = 0, Kvm = 0, Kop = 0, Kom = 0;
   std::vector<PBlock> pbs;
   int64_t maxpairs = 0, maxrows = 0, ldO = 0, ldt = 0;
-  int64_t kchunk = 0;
   int64_t n_epart = 0;
   // byte offsets into the workspace; SIZE_MAX = not present
   size_t o_LT = 0, o_LN = 0, o_tp = 0, o_tm = 0, o_tpT = 0, o_tmT = 0, o_bp = 0, o_bm = 0;
   size_t o_G = 0, o_gp = 0, o_gm = 0, o_Op = 0, o_Om = 0, o_Gp = 0, o_Gm = 0, o_Gt = 0, o_Gb = 0, o_E = 0;
+  size_t o_D = 0;
   size_t total = 0;
 };
 
@@ -419,13 +440,12 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
   P.Kj = rup(nj, 32);
   P.Kvp = rup(P.Pvp, 32); P.Kvm = rup(P.Pvm, 32);
   P.Kop = rup(P.Pop, 32); P.Kom = rup(P.Pom, 32);
-  int s = env_int("CC_BLOCK", 32);
+  int s = env_int("CC_BLOCK", 48);
   s = std::max(4, (s / 4) * 4);
   s = static_cast<int>(std::min<int64_t>(s, rup(v, 4)));
   P.s = s;
   P.nblk = static_cast<int>((v + s - 1) / s);
   P.nt = static_cast<int>((v + 31) / 32);
-  P.kchunk = rup(std::max(32, env_int("CC_KCHUNK", prec == CC_PREC_MIXED ? 4096 : 1 << 30)), 32);
   P.pbs.clear();
   int64_t off = 0;
   for (int al = 0; al < P.nblk; ++al)
@@ -476,6 +496,7 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
     P.o_Gm = take(static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
     P.o_Gt = take(mat_bytes(pr, P.maxrows, P.ldt));
     P.o_Gb = take(mat_bytes(pr, P.maxrows, P.ldt));
+    if (prec == CC_PREC_MIXED) P.o_D = take(static_cast<size_t>(nj) * v * v * 8);
   }
   P.o_E = take(static_cast<size_t>(P.n_epart) * 8);
   P.total = cur;
@@ -527,7 +548,7 @@ struct Profiler {
 static Profiler g_prof;
 
 template <typename F>
-static int profiled(const GemmOp& g, cudaStream_t s, F&& launch) {
+static int profiled(const GemmOp& g, cudaStream_t s, F&& launch, const GemmOp* g2) {
   bool on;
   {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -541,6 +562,7 @@ static int profiled(const GemmOp& g, cudaStream_t s, F&& launch) {
     e1 = g_prof.get();
     g_prof.pending.emplace_back(e0, e1);
     g_prof.flops += 2.0 * static_cast<double>(g.M) * static_cast<double>(g.N) * static_cast<double>(g.K);
+    if (g2) g_prof.flops += 2.0 * static_cast<double>(g2->M) * static_cast<double>(g2->N) * static_cast<double>(g2->K);
     g_prof.launches += 1;
   }
   cudaEventRecord(e0, s);
@@ -553,17 +575,15 @@ template <typename T>
 struct Path;
 template <>
 struct Path<double> {
+  using S = double;  // scratch element
   static constexpr int NP = 1;
-  static int gemm(const GemmOp& g, cudaStream_t s) {
-    return profiled(g, s, [&] { return gemm_f64(g, s); });
-  }
+  static constexpr bool mixed = false;
 };
 template <>
 struct Path<__nv_bfloat16> {
+  using S = float2;
   static constexpr int NP = 3;
-  static int gemm(const GemmOp& g, cudaStream_t s) {
-    return profiled(g, s, [&] { return gemm_mixed(g, s); });
-  }
+  static constexpr bool mixed = true;
 };
 
 template <typename T>
@@ -571,36 +591,57 @@ static T* at(char* ws, size_t off) {
   return reinterpret_cast<T*>(ws + off);
 }
 
-template <typename T>
-static GemmOp mk_gemm(const T* A, int64_t lda, int64_t a_rows, int64_t a_cols, int64_t a_piece, const T* B,
-                      int64_t ldb, int64_t b_rows, int64_t b_cols, int64_t b_piece, int64_t M, int64_t N, int64_t K,
-                      double* out, int64_t ldo, int atomic, int64_t kchunk, const Ctx& c) {
-  GemmOp g;
-  g.A = A; g.lda = lda; g.a_rows = a_rows; g.a_cols = a_cols; g.a_piece = a_piece;
-  g.B = B; g.ldb = ldb; g.b_rows = b_rows; g.b_cols = b_cols; g.b_piece = b_piece;
-  g.M = M; g.N = N; g.K = K; g.out = out; g.ldo = ldo; g.atomic = atomic; g.kchunk = kchunk;
-  g.status = c.status; g.timeout_ns = c.timeout_ns;
-  return g;
+// One contraction out[n*ldo + m] (= | +=) sum_k A[m][k] B[n][k] as an op
+// record; `acc` asks for accumulation into what the output holds.
+struct Gm {
+  const void* A; int64_t lda, a_rows, a_cols, a_piece;
+  const void* B; int64_t ldb, b_rows, b_cols, b_piece;
+  int64_t M, N, K;
+  void* out; int64_t ldo;
+  bool acc;
+};
+
+// K chunk for the FP64 path: whole K unless the launch would have fewer
+// than ~2 waves of CTAs on 152 SMs; then split K (chunks added atomically).
+static int64_t f64_kchunk(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  const int64_t target = 2 * 152;
+  if (tiles >= target) return K;
+  const int64_t splits = std::min<int64_t>((target + tiles - 1) / tiles, std::max<int64_t>(1, K / 256));
+  return std::max<int64_t>(32, rup((K + splits - 1) / splits, 32));
 }
 
-// K chunk for one contraction: the precision bound of the path, shrunk when
-// needed so that the launch has at least ~2 waves of CTAs on 152 SMs.
-static int64_t pick_kchunk(const Plan& P, int64_t M, int64_t N, int64_t K, bool want_split) {
-  int64_t kc = std::min<int64_t>(P.kchunk, K);
-  if (!want_split) return kc;
-  const int64_t bm = P.prec == CC_PREC_MIXED ? 128 : 64, bn = P.prec == CC_PREC_MIXED ? 128 : 64;
-  const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
-  const int64_t target = 2 * 152;
-  if (tiles < target) {
-    const int64_t splits = std::min<int64_t>((target + tiles - 1) / tiles, std::max<int64_t>(1, K / 256));
-    kc = std::min(kc, rup((K + splits - 1) / splits, 32));
+// Launch one group of up to two contractions of the same shape class.
+template <typename T>
+static void run_gemms(const Gm* g, int n, Ctx& c) {
+  std::vector<GemmOp> ops(n);
+  for (int i = 0; i < n; ++i) {
+    GemmOp& o = ops[i];
+    o.A = g[i].A; o.lda = g[i].lda; o.a_rows = g[i].a_rows; o.a_cols = g[i].a_cols; o.a_piece = g[i].a_piece;
+    o.B = g[i].B; o.ldb = g[i].ldb; o.b_rows = g[i].b_rows; o.b_cols = g[i].b_cols; o.b_piece = g[i].b_piece;
+    o.M = g[i].M; o.N = g[i].N; o.K = g[i].K; o.out = g[i].out; o.ldo = g[i].ldo;
+    o.status = c.status; o.timeout_ns = c.timeout_ns;
   }
-  return std::max<int64_t>(32, kc);
+  if (Path<T>::mixed) {
+    for (int i = 0; i < n; ++i) ops[i].mode = g[i].acc ? OUT_FF_ACCUM : OUT_FF_STORE;
+    c.check(profiled(ops[0], c.st, [&] { return gemm_mixed(ops.data(), n, c.st); }, n > 1 ? &ops[1] : nullptr));
+  } else {
+    for (int i = 0; i < n; ++i) {
+      GemmOp& o = ops[i];
+      o.kchunk = f64_kchunk(o.M, o.N, o.K);
+      const bool split = o.kchunk < o.K;
+      if (split && !g[i].acc)
+        c.cuda(cudaMemsetAsync(o.out, 0, static_cast<size_t>(o.N) * o.ldo * sizeof(double), c.st));
+      o.mode = (split || g[i].acc) ? OUT_F64_ATOMIC : OUT_F64_STORE;
+      c.check(profiled(o, c.st, [&] { return gemm_f64(o, c.st); }, nullptr));
+    }
+  }
 }
 
 template <typename T>
 static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, double* omega, double* D, double* E,
                        bool do_res, bool do_den, bool do_E, Ctx& c) {
+  using S = typename Path<T>::S;
   const int o = P.o, v = P.v, nj = P.nj, vp = P.vp;
   const int64_t vv = static_cast<int64_t>(v) * v;
   const int minus = P.minus;
@@ -621,15 +662,15 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
 
   // --- residual-side preparation
   T *LT = nullptr, *gp = nullptr, *gm = nullptr;
-  double *G = nullptr, *Op = nullptr, *Om = nullptr;
-  int64_t LT_piece = vv * P.Kj, g_piece_p = P.maxpairs * P.Kvp, g_piece_m = P.maxpairs * P.Kvm;
+  S *G = nullptr, *Op = nullptr, *Om = nullptr;
+  const int64_t LT_piece = vv * P.Kj, g_piece_p = P.maxpairs * P.Kvp, g_piece_m = P.maxpairs * P.Kvm;
   if (do_res) {
     LT = at<T>(ws, P.o_LT);
-    G = at<double>(ws, P.o_G);
+    G = at<S>(ws, P.o_G);
     gp = at<T>(ws, P.o_gp);
     gm = at<T>(ws, P.o_gm);
-    Op = at<double>(ws, P.o_Op);
-    Om = at<double>(ws, P.o_Om);
+    Op = at<S>(ws, P.o_Op);
+    Om = at<S>(ws, P.o_Om);
     k_prep_LT<T><<<dim3(static_cast<unsigned>((vv + 31) / 32), static_cast<unsigned>(P.Kj / 32)), dim3(32, 8), 0,
                    st>>>(sy.L_vv, nj, vv, LT, P.Kj, LT_piece);
     c.launched();
@@ -639,7 +680,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
 
   // --- density-side preparation
   T *LN = nullptr, *tpT = nullptr, *tmT = nullptr, *bp = nullptr, *bm = nullptr, *Gt = nullptr, *Gb = nullptr;
-  double *Gp = nullptr, *Gm = nullptr;
+  S *Gp = nullptr, *Gm_ = nullptr, *Dacc = nullptr;
   const int64_t LN_piece = static_cast<int64_t>(nj) * v * vp;
   const int64_t tpT_piece = P.Pvp * P.Kop, tmT_piece = P.Pvm * P.Kom;
   const int64_t bp_piece = P.Pvp * P.Kop, bm_piece = P.Pvp * P.Kom;
@@ -650,10 +691,13 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     tmT = at<T>(ws, P.o_tmT);
     bp = at<T>(ws, P.o_bp);
     bm = at<T>(ws, P.o_bm);
-    Gp = at<double>(ws, P.o_Gp);
-    Gm = at<double>(ws, P.o_Gm);
+    Gp = at<S>(ws, P.o_Gp);
+    Gm_ = at<S>(ws, P.o_Gm);
     Gt = at<T>(ws, P.o_Gt);
     Gb = at<T>(ws, P.o_Gb);
+    // D accumulates over pair blocks: in float-float scratch (mixed) or
+    // directly in the FP64 output (FP64 path)
+    Dacc = Path<T>::mixed ? at<S>(ws, P.o_D) : reinterpret_cast<S*>(D);
     k_prep_LN<T><<<2048, 256, 0, st>>>(sy.L_vv, nj, v, vp, LN, LN_piece);
     c.launched();
     c.cuda(cudaMemsetAsync(tpT, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
@@ -676,7 +720,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     }
     c.cuda(cudaMemsetAsync(Gt, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
     c.cuda(cudaMemsetAsync(Gb, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
-    c.cuda(cudaMemsetAsync(D, 0, static_cast<size_t>(nj) * vv * 8, st));
+    c.cuda(cudaMemsetAsync(Dacc, 0, static_cast<size_t>(nj) * vv * 8, st));
   }
 
   const unsigned ntp = static_cast<unsigned>(P.nt * (P.nt + 1) / 2);
@@ -685,71 +729,53 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     if (do_res) {
       // g-build: G[(b_l,d)][(a_l,c)] = sum_J L^J_ac L^J_bd
       const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
-      const int64_t kc = pick_kchunk(P, M, N, P.Kj, false);
-      if (kc < P.Kj) c.cuda(cudaMemsetAsync(G, 0, static_cast<size_t>(M) * N * 8, st));
-      c.check(Path<T>::gemm(mk_gemm<T>(LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, LT_piece,
-                                       LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, LT_piece, M, N,
-                                       P.Kj, G, M, 0, kc, c),
-                            st));
-      k_pack_g<T><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
+      const Gm g = {LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, LT_piece,
+                    LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, LT_piece,
+                    M, N, P.Kj, G, M, false};
+      run_gemms<T>(&g, 1, c);
+      k_pack_g<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
           G, M, v, b.a0, b.b0, b.nb, b.diag, P.nt, gp, P.Kvp, g_piece_p, gm, P.Kvm, g_piece_m, minus);
       c.launched();
-      // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]
-      c.cuda(cudaMemsetAsync(Op, 0, static_cast<size_t>(P.Pop) * P.ldO * 8, st));
-      c.check(Path<T>::gemm(mk_gemm<T>(gp, P.Kvp, b.npairs, P.Kvp, g_piece_p, tp, P.Kvp, P.Pop, P.Kvp, tp_piece,
-                                       b.npairs, P.Pop, P.Kvp, Op, P.ldO, 1,
-                                       pick_kchunk(P, b.npairs, P.Pop, P.Kvp, true), c),
-                            st));
-      if (minus) {
-        c.cuda(cudaMemsetAsync(Om, 0, static_cast<size_t>(P.Pom) * P.ldO * 8, st));
-        c.check(Path<T>::gemm(mk_gemm<T>(gm, P.Kvm, b.npairs, P.Kvm, g_piece_m, tm, P.Kvm, P.Pom, P.Kvm, tm_piece,
-                                         b.npairs, P.Pom, P.Kvm, Om, P.ldO, 1,
-                                         pick_kchunk(P, b.npairs, P.Pom, P.Kvm, true), c),
-                              st));
-      }
-      k_unpack_omega<<<static_cast<unsigned>(o2), 256, 0, st>>>(
+      // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]  (both signs in one launch)
+      const Gm lg[2] = {
+          {gp, P.Kvp, b.npairs, P.Kvp, g_piece_p, tp, P.Kvp, P.Pop, P.Kvp, tp_piece, b.npairs, P.Pop, P.Kvp, Op,
+           P.ldO, false},
+          {gm, P.Kvm, b.npairs, P.Kvm, g_piece_m, tm, P.Kvm, P.Pom, P.Kvm, tm_piece, b.npairs, P.Pom, P.Kvm, Om,
+           P.ldO, false}};
+      run_gemms<T>(lg, minus ? 2 : 1, c);
+      k_unpack_omega<S><<<static_cast<unsigned>(o2), 256, 0, st>>>(
           Op, Om, P.ldO, o, v, b.a0, b.b0, b.nb, b.diag, b.npairs, minus, omega, sy.tbar2,
           do_E ? epart + static_cast<int64_t>(ib) * o2 : nullptr);
       c.launched();
     }
     if (do_den) {
-      // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]
-      {
-        const int64_t kc = pick_kchunk(P, P.Pvp, b.npairs, P.Kop, false);
-        if (kc < P.Kop) c.cuda(cudaMemsetAsync(Gp, 0, static_cast<size_t>(b.npairs) * P.Kvp * 8, st));
-        c.check(Path<T>::gemm(mk_gemm<T>(tpT, P.Kop, P.Pvp, P.Kop, tpT_piece, bp + b.pair_off * P.Kop, P.Kop,
-                                         b.npairs, P.Kop, bp_piece, P.Pvp, b.npairs, P.Kop, Gp, P.Kvp, 0, kc, c),
-                              st));
-      }
-      if (minus) {
-        const int64_t kc = pick_kchunk(P, P.Pvm, b.npairs, P.Kom, false);
-        if (kc < P.Kom) c.cuda(cudaMemsetAsync(Gm, 0, static_cast<size_t>(b.npairs) * P.Kvm * 8, st));
-        c.check(Path<T>::gemm(mk_gemm<T>(tmT, P.Kom, P.Pvm, P.Kom, tmT_piece, bm + b.pair_off * P.Kom, P.Kom,
-                                         b.npairs, P.Kom, bm_piece, P.Pvm, b.npairs, P.Kom, Gm, P.Kvm, 0, kc, c),
-                              st));
-      }
-      k_unpack_gamma<T><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
-          Gp, Gm, P.Kvp, P.Kvm, v, vp, b.a0, b.b0, b.nb, b.diag, P.nt, minus, Gt, P.ldt, gt_piece, Gb, P.ldt,
+      // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]  (both signs in one launch)
+      const Gm gg[2] = {
+          {tpT, P.Kop, P.Pvp, P.Kop, tpT_piece, bp + b.pair_off * P.Kop, P.Kop, b.npairs, P.Kop, bp_piece, P.Pvp,
+           b.npairs, P.Kop, Gp, P.Kvp, false},
+          {tmT, P.Kom, P.Pvm, P.Kom, tmT_piece, bm + b.pair_off * P.Kom, P.Kom, b.npairs, P.Kom, bm_piece, P.Pvm,
+           b.npairs, P.Kom, Gm_, P.Kvm, false}};
+      run_gemms<T>(gg, minus ? 2 : 1, c);
+      k_unpack_gamma<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
+          Gp, Gm_, P.Kvp, P.Kvm, v, vp, b.a0, b.b0, b.nb, b.diag, P.nt, minus, Gt, P.ldt, gt_piece, Gb, P.ldt,
           gt_piece);
       c.launched();
-      // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd
-      {
-        const int64_t M = static_cast<int64_t>(b.na) * v, K = rup(static_cast<int64_t>(b.nb) * vp, 32);
-        c.check(Path<T>::gemm(mk_gemm<T>(Gt, P.ldt, M, P.ldt, gt_piece, LN + static_cast<int64_t>(b.b0) * vp,
-                                         static_cast<int64_t>(v) * vp, nj,
-                                         static_cast<int64_t>(v - b.b0) * vp, LN_piece, M, nj, K,
-                                         D + static_cast<int64_t>(b.a0) * v, vv, 1, pick_kchunk(P, M, nj, K, true), c),
-                              st));
-      }
-      if (!b.diag) {
-        const int64_t M = static_cast<int64_t>(b.nb) * v, K = rup(static_cast<int64_t>(b.na) * vp, 32);
-        c.check(Path<T>::gemm(mk_gemm<T>(Gb, P.ldt, M, P.ldt, gt_piece, LN + static_cast<int64_t>(b.a0) * vp,
-                                         static_cast<int64_t>(v) * vp, nj,
-                                         static_cast<int64_t>(v - b.a0) * vp, LN_piece, M, nj, K,
-                                         D + static_cast<int64_t>(b.b0) * v, vv, 1, pick_kchunk(P, M, nj, K, true), c),
-                              st));
-      }
+      // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd  (top and, off the diagonal, bottom)
+      const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 32);
+      const int64_t Mb = static_cast<int64_t>(b.nb) * v, Kb = rup(static_cast<int64_t>(b.na) * vp, 32);
+      const Gm dg[2] = {
+          {Gt, P.ldt, Mt, P.ldt, gt_piece, LN + static_cast<int64_t>(b.b0) * vp, static_cast<int64_t>(v) * vp, nj,
+           static_cast<int64_t>(v - b.b0) * vp, LN_piece, Mt, nj, Kt, Dacc + static_cast<int64_t>(b.a0) * v, vv,
+           true},
+          {Gb, P.ldt, Mb, P.ldt, gt_piece, LN + static_cast<int64_t>(b.a0) * vp, static_cast<int64_t>(v) * vp, nj,
+           static_cast<int64_t>(v - b.a0) * vp, LN_piece, Mb, nj, Kb, Dacc + static_cast<int64_t>(b.b0) * v, vv,
+           true}};
+      run_gemms<T>(dg, b.diag ? 1 : 2, c);
     }
+  }
+  if (do_den && Path<T>::mixed) {
+    k_ff_to_f64<<<4096, 256, 0, st>>>(reinterpret_cast<const float2*>(Dacc), D, static_cast<int64_t>(nj) * vv);
+    c.launched();
   }
   if (do_E && do_res) {
     k_sum_final<<<1, 1024, 0, st>>>(epart, static_cast<int64_t>(P.pbs.size()) * o2, E);

@@ -64,6 +64,82 @@ struct Store<__nv_bfloat16> {
   }
 };
 
+// ---------------------------------------------------------------- float-float
+// Intermediates of the mixed path are unevaluated sums hi + lo of two FP32
+// numbers (48 significant bits).  All arithmetic on them uses FP32 only:
+// GB300 runs FP64 arithmetic at about 1/1800 of its BF16 tensor rate, so
+// no FP64 instruction may sit in a per-element hot loop.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {  // needs |a| >= |b| or a = 0
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = ff_two_sum(a.x, b.x);
+  return ff_fast_two_sum(s.x, s.y + (a.y + b.y));
+}
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ff_scale(float2 a, float c) { return make_float2(a.x * c, a.y * c); }
+
+// x = hi + lo  ~=  p0 + p1 + p2, every step in FP32 (hi - p0 and r - p1 are exact)
+__device__ __forceinline__ Split3 split3_ff(float2 x) {
+  Split3 s;
+  s.p[0] = __float2bfloat16_rn(x.x);
+  const float r = (x.x - __bfloat162float(s.p[0])) + x.y;
+  s.p[1] = __float2bfloat16_rn(r);
+  s.p[2] = __float2bfloat16_rn(r - __bfloat162float(s.p[1]));
+  return s;
+}
+
+// Scratch arithmetic of the two paths: FP64 values (FP64 path) or
+// float-float values (mixed path).
+template <typename S>
+struct Ar;
+template <>
+struct Ar<double> {
+  using V = double;
+  static __device__ __forceinline__ V ld(const double* p, int64_t i) { return p[i]; }
+  static __device__ __forceinline__ V zero() { return 0.0; }
+  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+  static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
+  static __device__ __forceinline__ V scale(V a, float c) { return a * static_cast<double>(c); }
+  static __device__ __forceinline__ double to_d(V a) { return a; }
+};
+template <>
+struct Ar<float2> {
+  using V = float2;
+  static __device__ __forceinline__ V ld(const float2* p, int64_t i) { return p[i]; }
+  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ V add(V a, V b) { return ff_add(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return ff_add(a, ff_neg(b)); }
+  static __device__ __forceinline__ V scale(V a, float c) { return ff_scale(a, c); }
+  static __device__ __forceinline__ double to_d(V a) {
+    return static_cast<double>(a.x) + static_cast<double>(a.y);
+  }
+};
+
+// Operand store: FP64 path keeps the value, mixed path splits float-float
+// values into three BF16 pieces.
+template <typename T, typename V>
+struct Put;
+template <>
+struct Put<double, double> {
+  static __device__ __forceinline__ void put(double* base, int64_t idx, int64_t, double x) { base[idx] = x; }
+};
+template <>
+struct Put<__nv_bfloat16, float2> {
+  static __device__ __forceinline__ void put(__nv_bfloat16* base, int64_t idx, int64_t piece, float2 x) {
+    const Split3 s = split3_ff(x);
+    base[idx] = s.p[0];
+    base[idx + piece] = s.p[1];
+    base[idx + 2 * piece] = s.p[2];
+  }
+};
+
 // ---------------------------------------------------------------- pair index
 // Row-major upper triangle of an n x n index square.
 //   symmetric pairs  p <= q : k = p*(2n - p + 1)/2 + (q - p)
@@ -215,6 +291,23 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// 32 lanes x 16 columns (16 registers per thread), load and store.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

@@ -1,14 +1,18 @@
 // Internal contraction engine of the ladder library.
 //
-//   out[n * ldo + m]  (=|+=)  sum_{k < K} A[m][k] * B[n][k]      (m < M, n < N)
+//   out[n * ldo + m]  (= | +=)  sum_{k < K} A[m][k] * B[n][k]      (m < M, n < N)
 //
 // Both operands are K-major ("TN"): A is M x K, B is N x K, K contiguous.
 // The output is written transposed (M contiguous) so that a warp's lanes,
 // which hold consecutive rows m of the accumulator, store coalesced.
-// K is split into chunks of `kchunk`; each chunk is accumulated on its own
-// (FP32 in TMEM on the mixed path, FP64 on the FP64 path) and added into the
-// FP64 output with an atomic add when more than one chunk exists or when
-// `atomic` is set (the caller zeroes the output first).
+//
+// Mixed path (gemm_mixed): split-BF16 operands, one CTA per 128 x 128
+// output tile over the whole K, float-float output (float2 hi/lo) either
+// stored (OUT_FF_STORE) or added to what is there (OUT_FF_ACCUM, a plain
+// read-modify-write: tiles are owned by one CTA).  Up to two problems of
+// the same kind run in one launch (grid z selects the problem).
+// FP64 path (gemm_f64): FP64 operands and output; K may be split into
+// chunks that are added with FP64 atomics (OUT_F64_ATOMIC, caller zeroes).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -17,25 +21,27 @@
 
 namespace ccl {
 
+enum OutMode { OUT_F64_STORE = 0, OUT_F64_ATOMIC = 1, OUT_FF_STORE = 2, OUT_FF_ACCUM = 3 };
+
 struct GemmOp {
-  // A: rows a_rows (>= M is not required: rows past a_rows read as zero),
-  //    a_cols valid columns (columns past it read as zero), row pitch lda
-  //    elements; split-BF16 pieces are a_piece elements apart.
+  // A: rows a_rows (rows past it read as zero), a_cols valid columns
+  //    (columns past it read as zero), row pitch lda elements; split-BF16
+  //    pieces are a_piece elements apart.
   const void* A = nullptr;
   int64_t lda = 0, a_rows = 0, a_cols = 0, a_piece = 0;
   const void* B = nullptr;
   int64_t ldb = 0, b_rows = 0, b_cols = 0, b_piece = 0;
   int64_t M = 0, N = 0, K = 0;  // K: loop extent, a multiple of 32
-  double* out = nullptr;
+  void* out = nullptr;          // double* (FP64 modes) or float2* (FF modes)
   int64_t ldo = 0;
-  int atomic = 0;
-  int64_t kchunk = 0;  // multiple of 32; 0 = whole K in one chunk
+  int mode = OUT_F64_STORE;
+  int64_t kchunk = 0;           // FP64 path only: K per CTA (0 = whole K)
   Status* status = nullptr;
   uint64_t timeout_ns = 2000000000ull;
 };
 
 // Returns 0 or a negative CC_ERR_* code.
-int gemm_mixed(const GemmOp& op, cudaStream_t stream);
+int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream);
 int gemm_f64(const GemmOp& op, cudaStream_t stream);
 
 // Launch counter shared by every kernel launch of the library.

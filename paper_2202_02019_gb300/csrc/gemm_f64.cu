@@ -6,6 +6,8 @@
 // 4 x 2 DMMA tiles.  Operand tiles are staged through registers into a
 // double-buffered shared-memory ring (row pitch 20 doubles, which keeps
 // the fragment reads of each half-warp on distinct banks).
+#include <algorithm>
+
 #include "gemm.h"
 
 namespace ccl {
@@ -110,17 +112,18 @@ __global__ void __launch_bounds__(256) cc_gemm_f64_dmma(const double* __restrict
 
 int gemm_f64(const GemmOp& op, cudaStream_t stream) {
   if (op.M <= 0 || op.N <= 0 || op.K <= 0) return 0;
+  if (op.mode != OUT_F64_STORE && op.mode != OUT_F64_ATOMIC) return -1;
   if (op.M > (int64_t)FBM * 65535 || op.K > 2147483647LL) return -1;
   const int64_t kc = op.kchunk ? std::min<int64_t>(op.kchunk, op.K) : op.K;
   const int64_t nsplit = (op.K + kc - 1) / kc;
   if (nsplit > 65535) return -1;
-  const int atomic = (op.atomic || nsplit > 1) ? 1 : 0;
+  if (nsplit > 1 && op.mode != OUT_F64_ATOMIC) return -1;  // split chunks must be added atomically
   dim3 grid(static_cast<unsigned>((op.N + FBN - 1) / FBN), static_cast<unsigned>((op.M + FBM - 1) / FBM),
             static_cast<unsigned>(nsplit));
   cc_gemm_f64_dmma<<<grid, 256, 0, stream>>>(
       static_cast<const double*>(op.A), op.lda, op.a_rows, op.a_cols, static_cast<const double*>(op.B), op.ldb,
       op.b_rows, op.b_cols, static_cast<int>(op.M), static_cast<int>(op.N), static_cast<int>(op.K),
-      static_cast<int>(kc), op.out, op.ldo, atomic);
+      static_cast<int>(kc), static_cast<double*>(op.out), op.ldo, op.mode == OUT_F64_ATOMIC ? 1 : 0);
   count_launch();
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -4;
 }
