@@ -11,20 +11,22 @@
 // accumulator with a truncating (round-toward-zero) alignment, which biases
 // every output by about -1.7e-8 per step, growing linearly with K.  So:
 //   * the leading product a0b0 goes to its own TMEM accumulator H, which is
-//     restarted every WIN_KB k-blocks (128 terms); the drain warps add each
-//     window into an error-free FP32 two-sum (hi in registers, lo in TMEM),
-//     so the bias never spans more than 8 tensor-core steps;
+//     restarted every win_kb k-blocks (default 4: 128 terms), so the bias
+//     never spans more than 2*win_kb tensor-core steps; the drain warps add
+//     the window sums in FP32 (round to nearest, unbiased) and every FOLD
+//     windows fold that partial sum error-free into a two-sum (HI in
+//     registers, LO in TMEM);
 //   * the five small products (weight <= 2^-8 of the leading one) go to a
-//     second accumulator L, drained the same way every LWIN windows (4096
-//     terms); its truncation bias is scaled down by that weight.
+//     second accumulator L, drained the same way every 4096 terms; its
+//     truncation bias is scaled down by that weight.
 // H is double-buffered (H0, H1) so the drain of one window overlaps the
 // MMAs of the next; the MMA warp waits for the (rare) L drain.  One CTA
 // owns a 128 x 128 output tile over the whole K and writes the float-float
 // result hi + lo (or adds it to the float-float value already there).
 //
-// CTA = 10 warps: warp 0 issues TMA loads (one elected lane), warp 1 owns
-// TMEM and issues tcgen05.mma (one elected lane), warps 2-9 drain (warp w
-// reads TMEM lane quarter w%4, column half (w-2)/4).  Tile 128 x 128 x 32,
+// CTA = 18 warps: warp 0 issues TMA loads (one elected lane), warp 1 owns
+// TMEM and issues tcgen05.mma (one elected lane), warps 2-17 drain (warp w
+// reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile 128 x 128 x 32,
 // 4-stage smem ring (48 KB per stage: 3 A pieces + 3 B pieces, 64-byte
 // swizzle).  TMEM columns: H0 [0,128), H1 [128,256), L [256,384), lo [384,512).
 // Every wait is bounded (globaltimer) and latches CC_ERR_TIMEOUT.
@@ -32,6 +34,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -41,8 +44,8 @@ namespace ccl {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, STAGES = 4, NP = 3;
-constexpr int WIN_KB = 4;                 // k-blocks per H window (128 K terms)
-constexpr int LWIN = 32;                  // H windows per L segment (4096 K terms)
+constexpr int RASTER_GROUP = 8;           // m-tiles per raster group (L2 reuse of B panels)
+constexpr int FOLD = 8;                   // H windows summed in FP32 before the error-free fold
 constexpr int A_PIECE = BM * BK * 2;      // 8192 B
 constexpr int B_PIECE = BN * BK * 2;      // 8192 B
 constexpr int A_STAGE = NP * A_PIECE;     // 24576 B
@@ -51,8 +54,9 @@ constexpr int STAGE = A_STAGE + B_STAGE;  // 49152 B
 constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_H0 = 0, COL_H1 = 128, COL_L = 256, COL_LO = 384;
-constexpr int NTHREADS = 320;
-constexpr int NDRAIN = 8;                 // draining warps
+constexpr int NDRAIN = 16;                // draining warps (4 per TMEM lane quarter)
+constexpr int NTHREADS = (2 + NDRAIN) * 32;
+constexpr int DCOLS = BN / (NDRAIN / 4);  // accumulator columns per drain thread
 constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
 
 struct Prob {
@@ -63,6 +67,8 @@ struct Prob {
 };
 struct Probs {
   Prob p[2];
+  int win_kb;  // k-blocks per H window
+  int lwin;    // H windows per L segment
 };
 
 // piece indices of the six kept products; q = 5 is the leading a0b0
@@ -90,21 +96,37 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += e;
 }
 
-// Drain 64 TMEM columns of this thread's row into (hi, lo[TMEM]), 16 at a time.
-__device__ __forceinline__ void drain64(uint32_t src, uint32_t lo_addr, float (&hi)[64]) {
+// acc += DCOLS TMEM columns of this thread's row (plain round-to-nearest adds)
+__device__ __forceinline__ void add_cols(uint32_t src, float (&acc)[DCOLS]) {
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) {
-    uint32_t r[16], l[16];
+  for (int c = 0; c < DCOLS; c += 16) {
+    uint32_t r[16];
     tmem_ld16(src + c, r);
-    tmem_ld16(lo_addr + c, l);
     tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < 16; ++j) acc[c + j] += __uint_as_float(r[j]);
+  }
+}
+
+// (HI, LO[TMEM]) += acc error-free, then acc = 0
+__device__ __forceinline__ void fold_cols(uint32_t lo_addr, float (&acc)[DCOLS], float (&HI)[DCOLS]) {
+#pragma unroll
+  for (int c = 0; c < DCOLS; c += 8) {
+    uint32_t l[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7])
+                 : "r"(lo_addr + c));
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
       float lo = __uint_as_float(l[j]);
-      two_sum_acc(hi[c + j], lo, __uint_as_float(r[j]));
+      two_sum_acc(HI[c + j], lo, acc[c + j]);
+      acc[c + j] = 0.f;
       l[j] = __float_as_uint(lo);
     }
-    tmem_st16(lo_addr + c, l);
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(lo_addr + c),
+                 "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7])
+                 : "memory");
   }
   tmem_st_wait();
 }
@@ -112,8 +134,17 @@ __device__ __forceinline__ void drain64(uint32_t src, uint32_t lo_addr, float (&
 __global__ void __launch_bounds__(NTHREADS, 1)
     cc_gemm_split3_tc(const __grid_constant__ Probs P, Status* st, unsigned long long timeout_ns) {
   const Prob& pr = P.p[blockIdx.z];
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  if (n0 >= pr.N || m0 >= pr.M) return;  // whole CTA outside this problem
+  const int WIN_KB = P.win_kb, LWIN = P.lwin;
+  // grouped raster: consecutive CTAs sweep the n-tiles of RASTER_GROUP m-tiles
+  const int mt_n = (pr.M + BM - 1) / BM, nt_n = (pr.N + BN - 1) / BN;
+  const int lin = blockIdx.x;
+  if (lin >= mt_n * nt_n) return;  // whole CTA outside this problem
+  const int grp = lin / (RASTER_GROUP * nt_n);
+  const int gm0 = grp * RASTER_GROUP;
+  const int gsz = min(RASTER_GROUP, mt_n - gm0);
+  const int in_grp = lin - grp * RASTER_GROUP * nt_n;
+  const int m0 = (gm0 + in_grp % gsz) * BM;
+  const int n0 = (in_grp / gsz) * BN;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -222,20 +253,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else {
-    // drain warps: hi in registers, lo in TMEM columns [384, 512)
-    const int q = warp & 3;               // TMEM lane quarter
-    const int half = (warp - 2) >> 2;     // column half
+    // drain warps: window sums go into acc (FP32, round to nearest); every
+    // FOLD windows acc is added error-free into (HI registers, LO in TMEM
+    // columns [384, 512)).
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int cb = ((warp - 2) >> 2) * DCOLS;  // first accumulator column of this warp
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-    const uint32_t lo_addr = tmem + lane_off + COL_LO + half * 64;
-    float hi[64];
+    const uint32_t lo_addr = tmem + lane_off + COL_LO + cb;
+    float acc[DCOLS], HI[DCOLS];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) hi[j] = 0.f;
+    for (int j = 0; j < DCOLS; ++j) acc[j] = HI[j] = 0.f;
     {
-      uint32_t z[32];
+      uint32_t z[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) z[j] = 0u;
-      tmem_st32(lo_addr, z);
-      tmem_st32(lo_addr + 32, z);
+      for (int j = 0; j < 16; ++j) z[j] = 0u;
+#pragma unroll
+      for (int c = 0; c < DCOLS; c += 16) tmem_st16(lo_addr + c, z);
       tmem_st_wait();
     }
     bool ok = true;
@@ -246,28 +279,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ok = false;
         break;
       }
-      const bool lseg_end = (w + 1) % LWIN == 0 || w == nwin - 1;
-#pragma unroll 1
-      for (int pass = 0; pass < (lseg_end ? 2 : 1); ++pass) {
-        if (pass == 1) {
-          got = mbar_wait_bounded(lfull, (w / LWIN) & 1, abort_flag, timeout_ns);
-          if (!__all_sync(0xffffffffu, got)) {
-            ok = false;
-            break;
-          }
+      tc_fence_after();
+      add_cols(tmem + lane_off + (hb ? COL_H1 : COL_H0) + cb, acc);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&hempty[hb]);
+      if ((w + 1) % LWIN == 0 || w == nwin - 1) {
+        got = mbar_wait_bounded(lfull, (w / LWIN) & 1, abort_flag, timeout_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
         }
         tc_fence_after();
-        const uint32_t src = pass == 0 ? (hb ? COL_H1 : COL_H0) : COL_L;
-        drain64(tmem + lane_off + src + half * 64, lo_addr, hi);
+        add_cols(tmem + lane_off + COL_L + cb, acc);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          if (pass == 0)
-            mbar_arrive(&hempty[hb]);
-          else if (w != nwin - 1)
-            mbar_arrive(lempty);
-        }
+        if (lane == 0 && w != nwin - 1) mbar_arrive(lempty);
       }
+      if ((w + 1) % FOLD == 0 || w == nwin - 1) fold_cols(lo_addr, acc, HI);
     }
     ok = ok && !*abort_flag;
     if (!ok) {
@@ -275,16 +304,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else {
       const int row = m0 + q * 32 + lane;
 #pragma unroll
-      for (int c = 0; c < 64; c += 16) {
-        uint32_t l[16];
-        tmem_ld16(lo_addr + c, l);
+      for (int c = 0; c < DCOLS; c += 8) {
+        uint32_t l[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]),
+                       "=r"(l[7])
+                     : "r"(lo_addr + c));
         tmem_ld_wait();
         if (row < pr.M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + half * 64 + c + j;
+          for (int j = 0; j < 8; ++j) {
+            const int n = n0 + cb + c + j;
             if (n < pr.N) {
-              float2 v = ff_fast_two_sum(hi[c + j], __uint_as_float(l[j]));
+              float2 v = ff_fast_two_sum(HI[c + j], __uint_as_float(l[j]));
               float2* p = pr.out + static_cast<long long>(n) * pr.ldo + row;
               if (pr.mode == OUT_FF_ACCUM) v = ff_add(*p, v);
               *p = v;
@@ -303,6 +335,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+int env_int_(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return (v && *v) ? std::atoi(v) : dflt;
+}
 
 EncodeFn get_encode() {
   static EncodeFn fn = nullptr;
@@ -339,7 +376,9 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   if (nops < 1 || nops > 2) return -1;
   Probs P;
   memset(&P, 0, sizeof(P));
-  int64_t mt = 0, nt = 0;
+  int64_t tiles = 0;
+  P.win_kb = std::max(1, env_int_("CC_WIN_KB", 4));
+  P.lwin = std::max(1, 128 / P.win_kb);  // L segment of 128 k-blocks (4096 K terms)
   for (int i = 0; i < nops; ++i) {
     const GemmOp& op = ops[i];
     if (op.mode != OUT_FF_STORE && op.mode != OUT_FF_ACCUM) return -1;
@@ -356,8 +395,7 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
     P.p[i].N = static_cast<int>(op.N);
     P.p[i].K = static_cast<int>(op.K);
     P.p[i].mode = op.mode;
-    mt = std::max<int64_t>(mt, (op.M + BM - 1) / BM);
-    nt = std::max<int64_t>(nt, (op.N + BN - 1) / BN);
+    tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ((op.N + BN - 1) / BN));
   }
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
@@ -365,7 +403,8 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
     attr_err = cudaFuncSetAttribute(cc_gemm_split3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return -4;
-  dim3 grid(static_cast<unsigned>(nt), static_cast<unsigned>(mt), static_cast<unsigned>(nops));
+  if (tiles > 2147483647LL) return -1;
+  dim3 grid(static_cast<unsigned>(tiles), 1, static_cast<unsigned>(nops));
   cc_gemm_split3_tc<<<grid, NTHREADS, SMEM_BYTES, stream>>>(P, ops[0].status, ops[0].timeout_ns);
   count_launch();
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -4;
