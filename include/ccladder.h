@@ -4,15 +4,15 @@
  * Closed-shell problem statement (arXiv:2202.02019):
  *   Cholesky integrals (Sec. II.A):        g_acbd = sum_J L^J_ac L^J_bd
  *   ladder amplitudes:                      tau_ij^cd = t_ij^cd + t_i^c t_j^d
- *   ladder residual (Sec. II.C, A2 term):   Omega_ij^ab = sum_cd g_acbd tau_ij^cd
+ *   ladder residual (Sec. II.B, A2 term):   Omega_ij^ab = sum_cd g_acbd tau_ij^cd
  *   V^4 density (Eq. v4density, App. A):    Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd
- *   three-index density (Sec. II.D, the V^4 part of W-tilde, built with L):
+ *   three-index density (Sec. II.C, the V^4 part of W-tilde, built with L):
  *                                           D^J_ac = sum_bd Gamma_abcd L^J_bd
  *   Lagrangian slice (Eq. lagrangian):      E = sum_ijab tbar_ij^ab Omega_ij^ab
  * D carries no factor 2: Eq. (integral_contraction) has the 2, so dE/dL = 2 D.
  * Neither g nor Gamma is ever stored whole: both are built in tiles of
- * virtual-pair blocks and consumed at once (Sec. II.C / App. A storage policy),
- * using the symmetric/antisymmetric pair packing of Sec. II.C.
+ * virtual-pair blocks and consumed at once (Sec. II.B / App. A storage policy),
+ * using the symmetric/antisymmetric pair packing of Sec. II.B.
  *
  * Conventions shared by every entry point
  *   - All array arguments are DEVICE pointers to float64, C-contiguous:
@@ -88,14 +88,15 @@ typedef struct {
 size_t cc_ladder_workspace_size(const cc_ladder_system* sys, int n_sys,
                                 cc_precision p, int which);
 
-/* Ladder residual Omega_ij^ab = sum_cd g_acbd tau_ij^cd (Sec. II.C).
+/* Ladder residual Omega_ij^ab = sum_cd g_acbd tau_ij^cd (Sec. II.B).
  * omega[s] is a device [o][o][v][v] buffer per system. */
 int cc_ladder_residual(const cc_ladder_system* sys, int n_sys,
                        double* const* omega, cc_precision p,
                        void* ws, size_t ws_bytes, void* stream);
 
 /* Three-index density D^J_ac = sum_bd Gamma_abcd L^J_bd with
- * Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd (Eq. v4density, Sec. II.D).
+ * Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd (Eq. v4density of Sec. II.B; D is the
+ * V^4 part of the W-tilde intermediate of Sec. II.C).
  * D[s] is a device [nj][v][v] buffer per system; requires tbar2. */
 int cc_ladder_density(const cc_ladder_system* sys, int n_sys,
                       double* const* D, cc_precision p,

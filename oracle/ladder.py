@@ -9,13 +9,13 @@ Definitions (arXiv:2202.02019, closed shell, Mulliken notation):
 * Cholesky integrals, Sec. II.A (Cholesky expansion of (pq|rs)):
       g_acbd = (ac|bd) = sum_J L^J_ac L^J_bd
 * amplitudes entering the ladder:  tau_ij^cd = t_ij^cd + t_i^c t_j^d
-* ladder ("A2") residual term, Sec. II.C (Scuseria's A2 term of Omega):
+* ladder ("A2") residual term, Sec. II.B (Scuseria's A2 term of Omega):
       Omega_ij^ab = sum_cd g_acbd tau_ij^cd
 * V^4 density, Eq. (v4density) / App. A (O^(2)_abcd(L2, C2) with L2 = tbar2
   and C2 = tau; index map: the paper's (a,c | b,d) pairing is (a,b | c,d) here):
       Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd
 * its three-index contraction, the V^4 part of W^J_pq built with L in place
-  of Z (the W-tilde intermediate of Sec. II.D):
+  of Z (the W-tilde intermediate of Sec. II.C):
       D^J_ac = sum_bd Gamma_abcd L^J_bd
   D carries no factor 2; Eq. (integral_contraction) puts the 2 in front, so
   dE/dL = 2 D for pair-symmetric tbar and tau.
@@ -25,7 +25,7 @@ Definitions (arXiv:2202.02019, closed shell, Mulliken notation):
 Three independent formulations are provided: dense explicit-V^4 einsums
 (``*_dense``), row-blocked matmuls over the first virtual index that never
 form V^4 (``*_rows``), and the paper's symmetric/antisymmetric packed
-algorithm (``*_pm``, Sec. II.C: X^pm = X_ij +- X_ji, restricted loops
+algorithm (``*_pm``, Sec. II.B: X^pm = X_ij +- X_ji, restricted loops
 i>=j, a>=b, c>=d, net four-fold saving).
 
 Pins (tests/test_oracle.py): brute force vs rows vs packed, pair
@@ -63,7 +63,7 @@ def g_vvvv(L_vv):
 
 
 def residual_dense(L_vv, tau_):
-    """Omega_ij^ab = sum_cd g_acbd tau_ij^cd, explicit V^4 (Sec. II.C)."""
+    """Omega_ij^ab = sum_cd g_acbd tau_ij^cd, explicit V^4 (Sec. II.B)."""
     return np.einsum("acbd,ijcd->ijab", g_vvvv(L_vv), tau_)
 
 
@@ -73,7 +73,7 @@ def gamma_dense(tbar2, tau_):
 
 
 def density_dense(L_vv, tbar2, tau_):
-    """D^J_ac = sum_bd Gamma_abcd L^J_bd (W-tilde, Sec. II.D)."""
+    """D^J_ac = sum_bd Gamma_abcd L^J_bd (W-tilde, Sec. II.C)."""
     return np.einsum("abcd,Jbd->Jac", gamma_dense(tbar2, tau_), L_vv)
 
 
@@ -143,7 +143,7 @@ def sampled_rows(L_vv, t1, t2, tbar2, rows, cols=None):
 
 
 # --------------------------------------------------------------------------
-# symmetric / antisymmetric packed formulation (Sec. II.C)
+# symmetric / antisymmetric packed formulation (Sec. II.B)
 # --------------------------------------------------------------------------
 def _pm(X):
     """X^+- _ij = X_ij +- X_ji over the two leading (occupied) indices."""
@@ -167,7 +167,7 @@ def _expand(X, n1, n2, s1, s2):
 
 
 def residual_pm(L_vv, tau_):
-    """Packed ladder (Sec. II.C).  With X^pm_ij = X_ij +- X_ji:
+    """Packed ladder (Sec. II.B).  With X^pm_ij = X_ij +- X_ji:
 
         Omega^+[ab, ij] = sum_{c<=d} g+[ab, cd] tau+_ij^cd     (a<=b, i<=j)
         Omega^-[ab, ij] = sum_{c<d}  g-[ab, cd] tau-_ij^cd     (a<b,  i<j)
@@ -194,7 +194,7 @@ def residual_pm(L_vv, tau_):
 
 
 def gamma_pm(tbar2, tau_):
-    """Packed Gamma (Eq. v4density with the A2 trick of Sec. II.C):
+    """Packed Gamma (Eq. v4density with the A2 trick of Sec. II.B):
     Gamma_abcd = (Gamma+ + Gamma-)/4 with
     Gamma+[ab,cd] = sum_{i<=j} w_ij tbar+_ij^ab tau+_ij^cd  (w_ii=1, w_i<j=2)
     Gamma-[ab,cd] = sum_{i<j} 2 tbar-_ij^ab tau-_ij^cd,

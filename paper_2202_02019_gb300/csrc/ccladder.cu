@@ -4,7 +4,7 @@
 // Algorithm (arXiv:2202.02019, closed shell):
 //   Virtual rows are cut into blocks of `s`; a pair block (alpha <= beta)
 //   holds the pairs a<=b with a in block alpha and b in block beta.  Per pair
-//   block, with X^pm_ij = X_ij +- X_ji (Sec. II.C):
+//   block, with X^pm_ij = X_ij +- X_ji (Sec. II.B):
 //     g-build   G[(a,c),(b,d)] = sum_J L^J_ac L^J_bd           (Sec. II.A)
 //     pack      g+[ab,cd] = (G_cd + G_dc)(1/2 if c=d), g-[ab,cd] = G_cd - G_dc
 //     ladder    Omega^pm[ab,ij] = sum_{cd} g^pm[ab,cd] tau^pm_ij^cd  (i<=j, c<=d)
@@ -12,7 +12,7 @@
 //     Gamma     Gamma'^pm[ab,cd] = sum_ij w^pm_ij tbar^pm_ij^ab tau^pm_ij^cd
 //               (w+ = 1/4 (i=j), 1/2 (i<j); w- = 1/2), Gamma = Gamma'+ + Gamma'-
 //               extended by (anti)symmetry in ab and cd (Eq. v4density)
-//     density   D^J_xc += sum_{y,d} Gamma_xycd L^J_yd   (Sec. II.D, W-tilde)
+//     density   D^J_xc += sum_{y,d} Gamma_xycd L^J_yd   (Sec. II.C, W-tilde)
 //   so that neither g nor Gamma exists beyond one pair block.
 #include <algorithm>
 #include <atomic>
