@@ -63,7 +63,8 @@ enum {
   CC_ERR_DEVICE = -2,     /* current device is not sm_103                      */
   CC_ERR_WORKSPACE = -3,  /* ws_bytes smaller than cc_ladder_workspace_size()  */
   CC_ERR_CUDA = -4,       /* a CUDA call or launch failed (see strerror)       */
-  CC_ERR_TIMEOUT = -5     /* a bounded device wait gave up                     */
+  CC_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                     */
+  CC_ERR_SIZE = -6        /* request larger than a fixed-size device scratch   */
 };
 
 /* which-flags for cc_ladder_workspace_size */
@@ -128,6 +129,23 @@ int cc_ladder_update(const cc_ladder_system* sys, int n_sys,
  * latched in `ws` by earlier calls (CC_OK or CC_ERR_TIMEOUT), or
  * CC_ERR_CUDA if the stream reports an error. */
 int cc_ladder_status(void* ws, void* stream);
+
+/* Same value as cc_ladder_lagrangian with omega_opt given, for callers that
+ * cannot allocate device memory where they need E (a solver loop inside
+ * another framework's memory pool, or one that must not pay cudaMalloc's
+ * implicit synchronisation): no workspace argument and no allocation.  The
+ * paper has no counterpart; this is a library convenience.
+ * The partial sums live in a fixed device array of the library
+ * (64 systems x 1024 doubles = 512 KiB, held on every GPU that loads the
+ * library until the process exits).  At most 64 systems per call; more
+ * returns CC_ERR_SIZE.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (each call overwrites what it reads);
+ * calls that overlap on the GPU -- other streams, other host threads on the
+ * same device -- race on it and must be serialised by the caller. */
+int cc_ladder_lagrangian_noalloc(const cc_ladder_system* sys, int n_sys, double* E,
+                                 double* const* omega, void* stream);
 
 /* Testing hook for the bounded-wait machinery: launches one kernel that
  * spins on the device int *flag until it becomes non-zero or `timeout_ns`

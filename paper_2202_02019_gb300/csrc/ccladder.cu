@@ -981,6 +981,7 @@ const char* cc_ladder_strerror(int code) {
     case CC_ERR_DEVICE: return "current CUDA device is not sm_103 (GB300)";
     case CC_ERR_WORKSPACE: return "workspace smaller than cc_ladder_workspace_size()";
     case CC_ERR_TIMEOUT: return "a bounded device wait gave up (CC_ERR_TIMEOUT)";
+    case CC_ERR_SIZE: return "request exceeds the fixed device scratch (at most 64 systems per no-allocation call)";
     case CC_ERR_CUDA: {
       std::lock_guard<std::mutex> lk(g_err_mu);
       buf = "CUDA error: " + g_err_text;

@@ -69,6 +69,8 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_strerror.restype = ctypes.c_char_p
     lib.cc_ladder_launch_count.argtypes = []
     lib.cc_ladder_launch_count.restype = ctypes.c_longlong
+    lib.cc_ladder_lagrangian_noalloc.argtypes = [SYS, I, P, PP, VP]
+    lib.cc_ladder_lagrangian_noalloc.restype = I
     lib.cc_ladder_profile.argtypes = [I]
     lib.cc_ladder_profile.restype = None
     lib.cc_ladder_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -82,7 +84,7 @@ EXPORTS = (
     "cc_ladder_workspace_size", "cc_ladder_residual", "cc_ladder_density",
     "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
-    "cc_ladder_profile", "cc_ladder_profile_read",
+    "cc_ladder_profile", "cc_ladder_profile_read", "cc_ladder_lagrangian_noalloc",
 )
 
 
@@ -190,6 +192,16 @@ def cc_ladder_lagrangian(systems, omega=None, prec="mixed", ws=None, E=None, str
     _check(lib.cc_ladder_lagrangian(_arr(systems), len(systems), ctypes.c_void_p(E.data_ptr()), om,
                                     _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                     _stream(stream)))
+    return E
+
+
+def cc_ladder_lagrangian_noalloc(systems, omega, E=None, stream=None):
+    """E = sum tbar2 * Omega with no workspace and no device allocation (see the C header)."""
+    lib = load()
+    if E is None:
+        E = torch.empty(len(systems), dtype=torch.float64, device=systems[0].L_vv.device)
+    _check(lib.cc_ladder_lagrangian_noalloc(_arr(systems), len(systems), ctypes.c_void_p(E.data_ptr()),
+                                            _ptrs(omega), _stream(stream)))
     return E
 
 

@@ -71,3 +71,12 @@ def test_strerror():
     for code in (0, -1, -2, -3, -4, -5, -99):
         assert isinstance(lad.cc_ladder_strerror(code), str)
     assert "TIMEOUT" in lad.cc_ladder_strerror(-5)
+
+
+def test_noalloc_size_limit_is_host_checked():
+    lib = lad.load()
+    n = 65
+    arr = (lad.cc_ladder_system * n)(*[fake_sys(2, 3, 4) for _ in range(n)])
+    om = (ctypes.c_void_p * n)(*([0x6000] * n))
+    assert lib.cc_ladder_lagrangian_noalloc(arr, n, ctypes.c_void_p(0x7000), om, None) == -6
+    assert "64 systems" in lad.cc_ladder_strerror(-6)
