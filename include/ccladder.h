@@ -95,6 +95,16 @@ int cc_ladder_residual(const cc_ladder_system* sys, int n_sys,
                        double* const* omega, cc_precision p,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* Adjoint ladder: out_ij^cd = sum_ab tbar_ij^ab g_acbd = dE/dtau_ij^cd, the
+ * derivative of E = sum tbar . Omega with respect to the ladder amplitudes
+ * (Omega is linear in tau).  Computed as the ladder with L^J_ac replaced by
+ * L^J_ca applied to tbar2 (t1 and t2 are not read), so the g tiles are
+ * rebuilt, never stored.  out[s] is a device [o][o][v][v] buffer; requires
+ * tbar2.  Workspace: CC_WS_RESIDUAL. */
+int cc_ladder_residual_adjoint(const cc_ladder_system* sys, int n_sys,
+                               double* const* out, cc_precision p,
+                               void* ws, size_t ws_bytes, void* stream);
+
 /* Three-index density D^J_ac = sum_bd Gamma_abcd L^J_bd with
  * Gamma_abcd = sum_ij tbar_ij^ab tau_ij^cd (Eq. v4density of Sec. II.B; D is the
  * V^4 part of the W-tilde intermediate of Sec. II.C).

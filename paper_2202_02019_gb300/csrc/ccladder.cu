@@ -69,16 +69,18 @@ __device__ __forceinline__ void pb_pair(int64_t pr, int nb, int diag, int& al, i
 // preparation kernels
 // ---------------------------------------------------------------------------
 // L^J_ac ([nj][v*v]) -> LT[(a,c)][J] (J contiguous, zero for nj <= J < Kj)
+// (trans: read L^J_ca instead, for the adjoint ladder)
 template <typename T>
-__global__ void k_prep_LT(const double* __restrict__ L, int nj, int64_t v2, T* __restrict__ LT, int64_t Kj,
-                          int64_t piece) {
+__global__ void k_prep_LT(const double* __restrict__ L, int nj, int64_t v2, int v, int trans, T* __restrict__ LT,
+                          int64_t Kj, int64_t piece) {
   __shared__ double tile[32][33];
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
   const int j0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int J = j0 + i;
     const int64_t r = r0 + threadIdx.x;
-    tile[i][threadIdx.x] = (J < nj && r < v2) ? L[static_cast<int64_t>(J) * v2 + r] : 0.0;
+    const int64_t src = trans ? (r % v) * v + r / v : r;
+    tile[i][threadIdx.x] = (J < nj && r < v2) ? L[static_cast<int64_t>(J) * v2 + src] : 0.0;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
@@ -510,6 +512,7 @@ struct Ctx {
   cudaStream_t st;
   Status* status;
   uint64_t timeout_ns;
+  bool adjoint = false;  // residual of tbar2 with L^J transposed: sum_ab tbar_ij^ab g_acbd
   int err = 0;
   void check(int rc) {
     if (rc && !err) err = rc;
@@ -653,8 +656,9 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
   // --- tau^pm (both directions need it)
   c.cuda(cudaMemsetAsync(tp, 0, mat_bytes(P.prec, P.Pop, P.Kvp), st));
   if (minus) c.cuda(cudaMemsetAsync(tm, 0, mat_bytes(P.prec, P.Pom, P.Kvm), st));
-  k_pack_tau<T><<<dim3(v, static_cast<unsigned>(P.Pop)), 128, 0, st>>>(sy.t1, sy.t2, o, v, tp, P.Kvp, tp_piece, tm,
-                                                                      P.Kvm, tm_piece, minus);
+  k_pack_tau<T><<<dim3(v, static_cast<unsigned>(P.Pop)), 128, 0, st>>>(
+      c.adjoint ? nullptr : sy.t1, c.adjoint ? sy.tbar2 : sy.t2, o, v, tp, P.Kvp, tp_piece, tm, P.Kvm, tm_piece,
+      minus);
   c.launched();
 
   double* epart = at<double>(ws, P.o_E);
@@ -672,7 +676,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     Op = at<S>(ws, P.o_Op);
     Om = at<S>(ws, P.o_Om);
     k_prep_LT<T><<<dim3(static_cast<unsigned>((vv + 31) / 32), static_cast<unsigned>(P.Kj / 32)), dim3(32, 8), 0,
-                   st>>>(sy.L_vv, nj, vv, LT, P.Kj, LT_piece);
+                   st>>>(sy.L_vv, nj, vv, v, c.adjoint ? 1 : 0, LT, P.Kj, LT_piece);
     c.launched();
     c.cuda(cudaMemsetAsync(gp, 0, mat_bytes(P.prec, P.maxpairs, P.Kvp), st));
     if (minus) c.cuda(cudaMemsetAsync(gm, 0, mat_bytes(P.prec, P.maxpairs, P.Kvm), st));
@@ -821,9 +825,10 @@ static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int whic
 }
 
 static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
-               int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream) {
+               int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream,
+               bool adjoint = false) {
   if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED) return CC_ERR_ARG;
-  int rc = validate(sys, n_sys, den || want_E);
+  int rc = validate(sys, n_sys, den || want_E || adjoint);
   if (rc) return rc;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
   for (int i = 0; i < n_sys; ++i) {
@@ -840,6 +845,7 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
   c.st = static_cast<cudaStream_t>(stream);
   c.status = reinterpret_cast<Status*>(ws);
   c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
+  c.adjoint = adjoint;
   // every call starts from a clear status word; cc_ladder_status() reads it
   c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), c.st));
   for (int i = 0; i < n_sys && !c.err; ++i) {
@@ -873,6 +879,14 @@ int cc_ladder_residual(const cc_ladder_system* sys, int n_sys, double* const* om
   for (int i = 0; sys && i < n_sys; ++i)
     if (!omega[i]) return CC_ERR_ARG;
   return run(sys, n_sys, omega, nullptr, nullptr, p, CC_WS_RESIDUAL, true, false, false, ws, ws_bytes, stream);
+}
+
+int cc_ladder_residual_adjoint(const cc_ladder_system* sys, int n_sys, double* const* out, cc_precision p,
+                               void* ws, size_t ws_bytes, void* stream) {
+  if (!out) return CC_ERR_ARG;
+  for (int i = 0; sys && i < n_sys; ++i)
+    if (!out[i]) return CC_ERR_ARG;
+  return run(sys, n_sys, out, nullptr, nullptr, p, CC_WS_RESIDUAL, true, false, false, ws, ws_bytes, stream, true);
 }
 
 int cc_ladder_density(const cc_ladder_system* sys, int n_sys, double* const* D, cc_precision p, void* ws,

@@ -52,7 +52,7 @@ def load(build_if_missing: bool = True):
     PP = ctypes.POINTER(ctypes.c_void_p)
     lib.cc_ladder_workspace_size.argtypes = [SYS, I, I, I]
     lib.cc_ladder_workspace_size.restype = S
-    for name in ("cc_ladder_residual", "cc_ladder_density"):
+    for name in ("cc_ladder_residual", "cc_ladder_density", "cc_ladder_residual_adjoint"):
         getattr(lib, name).argtypes = [SYS, I, PP, I, VP, S, VP]
         getattr(lib, name).restype = I
     lib.cc_ladder_lagrangian.argtypes = [SYS, I, P, PP, I, VP, S, VP]
@@ -85,6 +85,7 @@ EXPORTS = (
     "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
     "cc_ladder_profile", "cc_ladder_profile_read", "cc_ladder_lagrangian_noalloc",
+    "cc_ladder_residual_adjoint",
 )
 
 
@@ -171,6 +172,16 @@ def cc_ladder_residual(systems, prec="mixed", ws=None, out=None, stream=None):
     out = out or [torch.empty_like(s.t2) for s in systems]
     _check(lib.cc_ladder_residual(_arr(systems), len(systems), _ptrs(out), _prec(prec),
                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def cc_ladder_residual_adjoint(systems, prec="mixed", ws=None, out=None, stream=None):
+    """dE/dtau_ij^cd = sum_ab tbar_ij^ab g_acbd (the adjoint ladder), one buffer per system."""
+    lib = load()
+    ws = _ws(systems, prec, CC_WS_RESIDUAL, ws)
+    out = out or [torch.empty_like(s.t2) for s in systems]
+    _check(lib.cc_ladder_residual_adjoint(_arr(systems), len(systems), _ptrs(out), _prec(prec),
+                                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return out
 
 
