@@ -219,7 +219,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2202_02019_gb300 import ladder as lad
-    from paper_2202_02019_gb300 import synth
+    from paper_2202_02019_gb300 import shard, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,11 +267,7 @@ def run_ours(args):
     lad.cc_ladder_profile(False)
     status = lad.cc_ladder_status(ws)
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t[0])
-    value = world * F / (ms_max * 1e-3) / 1e12
+    ms_max, value = shard.aggregate_step_time(ms, world, F)
 
     pk = peaks()
     gemm_ms_step = gemm_ms / args.steps
@@ -359,13 +355,81 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """24 independent systems of uneven size (o ~ U{6..40}, v ~ U{50..300}, N_J = 5v,
+    lambda_J = exp(-J/12)) in one graph-captured call, against one call per system."""
+    import torch
+    from paper_2202_02019_gb300 import autotune
+    from paper_2202_02019_gb300 import ladder as lad
+    from paper_2202_02019_gb300 import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lad.load()
+    sizes = synth.batch_sizes(24, seed=2202)
+    systems = []
+    for k, (o, v, nj) in enumerate(sizes):
+        d = synth.make_pair_torch(o, v, nj, 12.0, seed=2202 + 100 * k, device="cuda")
+        systems.append(lad.System(L_vv=d["L_vv"], t2=d["t2"], t1=d["t1"], tbar2=d["tbar2"], eps=d["eps"]))
+        del d
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    F = sum(counted_flops(o, v, nj) for o, v, nj in sizes)
+    tuned = autotune.tune(systems, prec="mixed", reps=1) if args.autotune else {"block": 0, "win": 0, "source": "default"}
+    ws = lad.workspace(systems, "mixed")
+    om = [torch.empty_like(s.t2) for s in systems]
+    D = [torch.empty_like(s.L_vv) for s in systems]
+    E = torch.empty(len(systems), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_by_one():
+        for k, sd in enumerate(systems):
+            lad.cc_ladder_step([sd], prec="mixed", ws=ws, omega=[om[k]], D=[D[k]], E=E[k:k + 1], stream=stream)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_seq = timed(one_by_one)
+    ref = [x.clone() for x in om[:2]]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lad.cc_ladder_step(systems, prec="mixed", ws=ws, omega=om, D=D, E=E)
+    n0 = lad.cc_ladder_launch_count()
+    with Clocks(0) as clk:
+        ms_graph = timed(g.replay)
+    same = all(torch.equal(a, b) for a, b in zip(ref, om[:2]))
+    line = {
+        "metric": "ladder Omega + D^J useful TFLOP/s, 24-system uneven batch (mixed path)",
+        "value": F / (ms_graph * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3 split (FP32 accumulate, FP64 reductions)",
+        "data": "synthetic (seeded, device generator)",
+        "config": {"workload": "batch24 o~U{6..40} v~U{50..300} nj=5v", "global_batch": 24,
+                   "sizes": sizes, "counted_flops": F, "tuning": tuned},
+        "one_call_per_system_ms": ms_seq, "graph_over_one_by_one": ms_seq / ms_graph,
+        "graph_equals_one_by_one": same, "clocks": clk.summary(),
+        "device_status": lad.cc_ladder_status(ws),
+    }
+    print(json.dumps(line), flush=True)
+    lad.cc_ladder_set_tuning(0, 0)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="retinal", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="retinal", choices=sorted(WORKLOADS) + ["batch24"])
+    ap.add_argument("--autotune", action="store_true", help="batch24: pick tuning knobs with the autotuner")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, oracle sample and small-config legs")
     ap.add_argument("--no-small", action="store_true", help="skip the small-config FP64-vs-mixed leg")
     args = ap.parse_args()
@@ -373,6 +437,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch24":
+        return run_batch(args)
     return run_ours(args)
 
 

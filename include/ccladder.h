@@ -168,6 +168,18 @@ int cc_ladder_debug_wait(const int* flag, long long timeout_ns, void* ws,
  * last CUDA error seen by the library is appended. */
 const char* cc_ladder_strerror(int code);
 
+/* Tuning knobs, process-wide, for calls made afterwards (0 = default):
+ *   block_edge   virtual rows per pair block (multiple of 4, <= 256; default
+ *                48).  Sets the scratch size: size workspaces after changing it.
+ *   win_kblocks  mixed path only: the leading-piece product is re-started every
+ *                win_kblocks * 32 K-terms (1, 2, 4 or 8; default 4).  Smaller
+ *                windows lower the truncation bias of the tensor-core FP32
+ *                accumulation (about 2e-7 relative at 2 vs 3.5e-7 at 4 for the
+ *                retinal-scale system) at some speed.
+ * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
+ * on other host threads. */
+int cc_ladder_set_tuning(int block_edge, int win_kblocks);
+
 /* Kernel launches issued by the calls above since the library was loaded
  * (a host-side counter). */
 long long cc_ladder_launch_count(void);

@@ -32,6 +32,15 @@ namespace ccl {
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
 
+// Process-wide tuning (cc_ladder_set_tuning); 0 = default.
+static std::atomic<int> g_tune_block{0}, g_tune_win{0};
+int tuned_win_kb() {
+  const int w = g_tune_win.load();
+  if (w > 0) return w;
+  const char* e = std::getenv("CC_WIN_KB");
+  return (e && *e) ? std::max(1, std::atoi(e)) : 4;
+}
+
 static std::mutex g_err_mu;
 static std::string g_err_text;
 static void note_cuda(cudaError_t e) {
@@ -442,7 +451,7 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
   P.Kj = rup(nj, 32);
   P.Kvp = rup(P.Pvp, 32); P.Kvm = rup(P.Pvm, 32);
   P.Kop = rup(P.Pop, 32); P.Kom = rup(P.Pom, 32);
-  int s = env_int("CC_BLOCK", 48);
+  int s = g_tune_block.load() > 0 ? g_tune_block.load() : env_int("CC_BLOCK", 48);
   s = std::max(4, (s / 4) * 4);
   s = static_cast<int>(std::min<int64_t>(s, rup(v, 4)));
   P.s = s;
@@ -1006,6 +1015,15 @@ const char* cc_ladder_strerror(int code) {
 }
 
 long long cc_ladder_launch_count(void) { return g_launches.load(); }
+
+int cc_ladder_set_tuning(int block_edge, int win_kblocks) {
+  if (block_edge < 0 || (block_edge > 0 && (block_edge % 4 || block_edge > 256))) return CC_ERR_ARG;
+  if (win_kblocks < 0 || (win_kblocks > 0 && (win_kblocks > 8 || (win_kblocks & (win_kblocks - 1)))))
+    return CC_ERR_ARG;
+  g_tune_block.store(block_edge);
+  g_tune_win.store(win_kblocks);
+  return CC_OK;
+}
 
 void cc_ladder_profile(int enable) {
   std::lock_guard<std::mutex> lk(g_prof.mu);

@@ -47,4 +47,7 @@ int gemm_f64(const GemmOp& op, cudaStream_t stream);
 // Launch counter shared by every kernel launch of the library.
 void count_launch(int n = 1);
 
+// Leading-product window of the mixed contraction, in k-blocks of 32.
+int tuned_win_kb();
+
 }  // namespace ccl

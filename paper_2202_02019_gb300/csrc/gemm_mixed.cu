@@ -336,10 +336,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 
-int env_int_(const char* name, int dflt) {
-  const char* v = std::getenv(name);
-  return (v && *v) ? std::atoi(v) : dflt;
-}
 
 EncodeFn get_encode() {
   static EncodeFn fn = nullptr;
@@ -377,7 +373,7 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   Probs P;
   memset(&P, 0, sizeof(P));
   int64_t tiles = 0;
-  P.win_kb = std::max(1, env_int_("CC_WIN_KB", 4));
+  P.win_kb = tuned_win_kb();
   P.lwin = std::max(1, 128 / P.win_kb);  // L segment of 128 k-blocks (4096 K terms)
   for (int i = 0; i < nops; ++i) {
     const GemmOp& op = ops[i];

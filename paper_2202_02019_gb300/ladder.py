@@ -71,6 +71,8 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_launch_count.restype = ctypes.c_longlong
     lib.cc_ladder_lagrangian_noalloc.argtypes = [SYS, I, P, PP, VP]
     lib.cc_ladder_lagrangian_noalloc.restype = I
+    lib.cc_ladder_set_tuning.argtypes = [I, I]
+    lib.cc_ladder_set_tuning.restype = I
     lib.cc_ladder_profile.argtypes = [I]
     lib.cc_ladder_profile.restype = None
     lib.cc_ladder_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -85,7 +87,7 @@ EXPORTS = (
     "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
     "cc_ladder_profile", "cc_ladder_profile_read", "cc_ladder_lagrangian_noalloc",
-    "cc_ladder_residual_adjoint",
+    "cc_ladder_residual_adjoint", "cc_ladder_set_tuning",
 )
 
 
@@ -262,3 +264,8 @@ def cc_ladder_profile_read():
     ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
     _check(load().cc_ladder_profile_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
     return ms.value, n.value, fl.value
+
+
+def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):
+    """Process-wide tuning knobs (0 = default); see the C header."""
+    _check(load().cc_ladder_set_tuning(int(block_edge), int(win_kblocks)))
