@@ -444,13 +444,14 @@ static size_t mat_bytes(int prec, int64_t R, int64_t C) {
 static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) {
   const int64_t o = sy.o, v = sy.v, nj = sy.nj;
   P.o = sy.o; P.v = sy.v; P.nj = sy.nj; P.prec = prec;
-  P.vp = static_cast<int>(rup(v, 8));
+  P.vp = static_cast<int>(rup(v, 16));  // s * vp is then a multiple of 64 (the contraction's K step)
   P.Pvp = v * (v + 1) / 2; P.Pvm = v * (v - 1) / 2;
   P.Pop = o * (o + 1) / 2; P.Pom = o * (o - 1) / 2;
   P.minus = (P.Pvm > 0 && P.Pom > 0) ? 1 : 0;
-  P.Kj = rup(nj, 32);
-  P.Kvp = rup(P.Pvp, 32); P.Kvm = rup(P.Pvm, 32);
-  P.Kop = rup(P.Pop, 32); P.Kom = rup(P.Pom, 32);
+  // contraction dimensions padded to the mixed engine's K step (64) with zeros
+  P.Kj = rup(nj, 64);
+  P.Kvp = rup(P.Pvp, 64); P.Kvm = rup(P.Pvm, 64);
+  P.Kop = rup(P.Pop, 64); P.Kom = rup(P.Pom, 64);
   int s = g_tune_block.load() > 0 ? g_tune_block.load() : env_int("CC_BLOCK", 48);
   s = std::max(4, (s / 4) * 4);
   s = static_cast<int>(std::min<int64_t>(s, rup(v, 4)));
@@ -774,8 +775,8 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
           gt_piece);
       c.launched();
       // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd  (top and, off the diagonal, bottom)
-      const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 32);
-      const int64_t Mb = static_cast<int64_t>(b.nb) * v, Kb = rup(static_cast<int64_t>(b.na) * vp, 32);
+      const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 64);
+      const int64_t Mb = static_cast<int64_t>(b.nb) * v, Kb = rup(static_cast<int64_t>(b.na) * vp, 64);
       const Gm dg[2] = {
           {Gt, P.ldt, Mt, P.ldt, gt_piece, LN + static_cast<int64_t>(b.b0) * vp, static_cast<int64_t>(v) * vp, nj,
            static_cast<int64_t>(v - b.b0) * vp, LN_piece, Mt, nj, Kt, Dacc + static_cast<int64_t>(b.a0) * v, vv,

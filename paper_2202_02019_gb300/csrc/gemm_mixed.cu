@@ -11,8 +11,8 @@
 // accumulator with a truncating (round-toward-zero) alignment, which biases
 // every output by about -1.7e-8 per step, growing linearly with K.  So:
 //   * the leading product a0b0 goes to its own TMEM accumulator H, which is
-//     restarted every win_kb k-blocks (default 4: 128 terms), so the bias
-//     never spans more than 2*win_kb tensor-core steps; the drain warps add
+//     restarted every 128 K terms by default (tunable), so the bias
+//     never spans more than 8 tensor-core steps; the drain warps add
 //     the window sums in FP32 (round to nearest, unbiased) and every FOLD
 //     windows fold that partial sum error-free into a two-sum (HI in
 //     registers, LO in TMEM);
@@ -26,9 +26,9 @@
 //
 // CTA = 18 warps: warp 0 issues TMA loads (one elected lane), warp 1 owns
 // TMEM and issues tcgen05.mma (one elected lane), warps 2-17 drain (warp w
-// reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile 128 x 128 x 32,
-// 4-stage smem ring (48 KB per stage: 3 A pieces + 3 B pieces, 64-byte
-// swizzle).  TMEM columns: H0 [0,128), H1 [128,256), L [256,384), lo [384,512).
+// reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile 128 x 128 x 64,
+// 2-stage smem ring (96 KB per stage: 3 A pieces + 3 B pieces, 128-byte
+// swizzle: 128-byte TMA rows move operands ~1.2x faster than 64-byte ones).  TMEM columns: H0 [0,128), H1 [128,256), L [256,384), lo [384,512).
 // Every wait is bounded (globaltimer) and latches CC_ERR_TIMEOUT.
 #include <cudaTypedefs.h>
 
@@ -43,14 +43,19 @@
 namespace ccl {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32, STAGES = 4, NP = 3;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, NP = 3;
 constexpr int RASTER_GROUP = 8;           // m-tiles per raster group (L2 reuse of B panels)
+#ifndef CC_GEMM_CLUSTER
+#define CC_GEMM_CLUSTER 2
+#endif
+constexpr int CLUSTER = CC_GEMM_CLUSTER;  // CTAs sharing one A tile (TMA multicast); 1 or 2
 constexpr int FOLD = 8;                   // H windows summed in FP32 before the error-free fold
-constexpr int A_PIECE = BM * BK * 2;      // 8192 B
-constexpr int B_PIECE = BN * BK * 2;      // 8192 B
-constexpr int A_STAGE = NP * A_PIECE;     // 24576 B
-constexpr int B_STAGE = NP * B_PIECE;     // 24576 B
-constexpr int STAGE = A_STAGE + B_STAGE;  // 49152 B
+constexpr int A_PIECE = BM * BK * 2;      // 16384 B
+constexpr int A_HALF = A_PIECE / CLUSTER; // bytes of one piece's row slice
+constexpr int B_PIECE = BN * BK * 2;      // 16384 B
+constexpr int A_STAGE = NP * A_PIECE;     // 49152 B
+constexpr int B_STAGE = NP * B_PIECE;     // 49152 B
+constexpr int STAGE = A_STAGE + B_STAGE;  // 98304 B
 constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_H0 = 0, COL_H1 = 128, COL_L = 256, COL_LO = 384;
@@ -60,7 +65,7 @@ constexpr int DCOLS = BN / (NDRAIN / 4);  // accumulator columns per drain threa
 constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
 
 struct Prob {
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb;  // ta: A box {32, 128/CLUSTER, 1} (one piece, one row slice); tb: B box {32, 128, 3}
   float2* out;
   long long ldo;
   int M, N, K, mode;
@@ -137,14 +142,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int WIN_KB = P.win_kb, LWIN = P.lwin;
   // grouped raster: consecutive CTAs sweep the n-tiles of RASTER_GROUP m-tiles
   const int mt_n = (pr.M + BM - 1) / BM, nt_n = (pr.N + BN - 1) / BN;
-  const int lin = blockIdx.x;
-  if (lin >= mt_n * nt_n) return;  // whole CTA outside this problem
-  const int grp = lin / (RASTER_GROUP * nt_n);
+  // Clusters of CLUSTER CTAs share one m-tile (its A tile is multicast) and
+  // take adjacent n-tiles; a CTA whose n-tile is past N computes masked zeros.
+  const int np_n = (nt_n + CLUSTER - 1) / CLUSTER;  // n-tile groups
+  const int crank = static_cast<int>(cluster_ctarank());
+  const int lin = blockIdx.x / CLUSTER;             // cluster index (uniform in the cluster)
+  if (lin >= mt_n * np_n) return;                   // whole cluster outside this problem
+  const int grp = lin / (RASTER_GROUP * np_n);
   const int gm0 = grp * RASTER_GROUP;
   const int gsz = min(RASTER_GROUP, mt_n - gm0);
-  const int in_grp = lin - grp * RASTER_GROUP * nt_n;
+  const int in_grp = lin - grp * RASTER_GROUP * np_n;
   const int m0 = (gm0 + in_grp % gsz) * BM;
-  const int n0 = (in_grp / gsz) * BN;
+  const int n0 = ((in_grp / gsz) * CLUSTER + crank) * BN;
+  const uint16_t cmask = static_cast<uint16_t>((1u << CLUSTER) - 1u);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -164,7 +174,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CLUSTER);  // one MMA commit from each CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&hfull[b], 1);
@@ -183,6 +193,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // peers' barriers are initialised before any multicast or remote arrive
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -196,8 +207,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         uint8_t* sa = smem + s * STAGE;
-        mbar_expect_tx(&full[s], STAGE);
-        tma_load_3d(&pr.ta, &full[s], sa, kb * BK, m0, 0);
+        mbar_expect_tx(&full[s], STAGE);  // own B + every CTA's slice of A
+        // this CTA's row slice of the shared A tile, to every CTA of the cluster
+#pragma unroll
+        for (int pc = 0; pc < NP; ++pc)
+          tma_load_3d_mc(&pr.ta, &full[s], sa + pc * A_PIECE + crank * A_HALF, kb * BK,
+                         m0 + crank * (BM / CLUSTER), pc, cmask);
         tma_load_3d(&pr.tb, &full[s], sa + A_STAGE, kb * BK, n0, 0);
       }
     }
@@ -237,15 +252,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int q = 0; q < 6; ++q) {
               int pa, pb;
               product_pieces(q, pa, pb);
-              const uint64_t ad = sdesc_k_sw64(a_base + pa * A_PIECE + ks * 32);
-              const uint64_t bd = sdesc_k_sw64(b_base + pb * B_PIECE + ks * 32);
+              const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
+              const uint64_t bd = sdesc_k_sw128(b_base + pb * B_PIECE + ks * 32);
               if (q == 5)
                 umma_f16(tmem + hcol, ad, bd, IDESC, first ? 0u : 1u);
               else
                 umma_f16(tmem + COL_L, ad, bd, IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
             }
           }
-          umma_commit(&empty[s]);
+          umma_commit_mc(&empty[s], cmask);  // releases the stage in every CTA it was written to
         }
         umma_commit(&hfull[hb]);
         if ((w + 1) % LWIN == 0 || w == nwin - 1) umma_commit(lfull);
@@ -328,6 +343,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // no CTA leaves while a peer may still arrive on its barriers
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
@@ -353,15 +369,16 @@ EncodeFn get_encode() {
 
 // 3-D map over the piece-stacked BF16 matrix: dims {cols, rows, 3 pieces}.
 bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int64_t piece,
-              int box_rows) {
+              int box_rows, int box_pieces = 3) {
   EncodeFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows), 3};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(piece) * 2};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows), 3};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows),
+                       static_cast<cuuint32_t>(box_pieces)};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -373,8 +390,8 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   Probs P;
   memset(&P, 0, sizeof(P));
   int64_t tiles = 0;
-  P.win_kb = tuned_win_kb();
-  P.lwin = std::max(1, 128 / P.win_kb);  // L segment of 128 k-blocks (4096 K terms)
+  P.win_kb = std::max(1, tuned_win_kb() * 32 / BK);  // window given in 32-term units
+  P.lwin = std::max(1, (4096 / BK) / P.win_kb);      // L segment of 4096 K terms
   for (int i = 0; i < nops; ++i) {
     const GemmOp& op = ops[i];
     if (op.mode != OUT_FF_STORE && op.mode != OUT_FF_ACCUM) return -1;
@@ -383,7 +400,7 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
       return -1;
     if ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.B)) & 15) return -1;
     if ((op.lda | op.ldb | op.a_piece | op.b_piece) & 7) return -1;
-    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM)) return -4;
+    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM / CLUSTER, 1)) return -4;
     if (!make_map(&P.p[i].tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN)) return -4;
     P.p[i].out = static_cast<float2*>(op.out);
     P.p[i].ldo = op.ldo;
@@ -391,7 +408,8 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
     P.p[i].N = static_cast<int>(op.N);
     P.p[i].K = static_cast<int>(op.K);
     P.p[i].mode = op.mode;
-    tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ((op.N + BN - 1) / BN));
+    const int64_t ngrp = ((op.N + BN - 1) / BN + CLUSTER - 1) / CLUSTER;
+    tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ngrp * CLUSTER);
   }
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
@@ -400,8 +418,20 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   });
   if (attr_err != cudaSuccess) return -4;
   if (tiles > 2147483647LL) return -1;
-  dim3 grid(static_cast<unsigned>(tiles), 1, static_cast<unsigned>(nops));
-  cc_gemm_split3_tc<<<grid, NTHREADS, SMEM_BYTES, stream>>>(P, ops[0].status, ops[0].timeout_ns);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(static_cast<unsigned>(tiles), 1, static_cast<unsigned>(nops));
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, cc_gemm_split3_tc, P, ops[0].status, ops[0].timeout_ns) != cudaSuccess) return -4;
   count_launch();
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -4;
 }
