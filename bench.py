@@ -33,7 +33,13 @@ WORKLOADS = {
     "small": (24, 180, 900, 150.0),
     "grad": (30, 250, 1200, 200.0),
 }
-METRIC = "ladder Omega + D^J useful TFLOP/s (mixed split-BF16 path), o78/v650/NJ4000"
+METRIC = "ladder Omega + D^J useful TFLOP/s (mixed-precision path), o78/v650/NJ4000"
+# products per useful product and the arithmetic each --prec runs in
+PREC = {
+    "mixed": (6, "bf16x3 split (FP32 accumulate, FP64 reductions)"),
+    "fp16x2": (3, "fp16x2 scaled split (FP32 accumulate, FP64 reductions)"),
+    "fp64": (1, "f64 (DMMA)"),
+}
 
 
 def counted_flops(o, v, nj):
@@ -191,7 +197,7 @@ def fp64_vs_mixed_small(lad, synth, torch):
     D_ref = O.density_rows(s.L_vv, tb2, tt, rows)
     F = counted_flops(o, v, nj)
     outs = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp16x2", "fp64"):
         ws = lad.workspace([sd], prec)
         om, D, E = lad.cc_ladder_step([sd], prec=prec, ws=ws)
         torch.cuda.synchronize()
@@ -211,6 +217,9 @@ def fp64_vs_mixed_small(lad, synth, torch):
     res["mixed_vs_fp64"] = {"rel_err_omega": rel(omm.cpu(), om64.cpu()), "rel_err_D": rel(Dm.cpu(), D64.cpu()),
                             "rel_err_E": abs(Em - E64) / abs(E64)}
     res["speedup_mixed_over_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    o16 = outs["fp16x2"]
+    res["fp16x2_vs_fp64"] = {"rel_err_omega": rel(o16[0].cpu(), om64.cpu()), "rel_err_D": rel(o16[1].cpu(), D64.cpu()),
+                             "rel_err_E": abs(o16[2] - E64) / abs(E64)}
     return res
 
 
@@ -234,14 +243,14 @@ def run_ours(args):
     sd = lad.System(L_vv=d["L_vv"], t2=d["t2"], t1=d["t1"], tbar2=d["tbar2"], eps=d["eps"])
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    ws = lad.workspace([sd], "mixed")
+    ws = lad.workspace([sd], args.prec)
     om = [torch.empty_like(sd.t2)]
     D = [torch.empty_like(sd.L_vv)]
     E = torch.empty(1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        lad.cc_ladder_step([sd], prec="mixed", ws=ws, omega=om, D=D, E=E, stream=stream)
+        lad.cc_ladder_step([sd], prec=args.prec, ws=ws, omega=om, D=D, E=E, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -272,10 +281,17 @@ def run_ours(args):
     pk = peaks()
     gemm_ms_step = gemm_ms / args.steps
     achieved = F / (gemm_ms_step * 1e-3) / 1e12
-    peak_useful = pk["bf16_sustained"] / 6.0
+    nprod = PREC[args.prec][0]
+    if args.prec == "fp64":
+        peak_useful, basis = 1.25, "nominal FP64 tensor rate (not measured)"
+    else:
+        # FP16 and BF16 share the dense tensor rate: the measured BF16 figure serves both
+        peak_useful = pk["bf16_sustained"] / nprod
+        basis = f"{pk['source']} sustained BF16 (= FP16 rate) / {nprod} products"
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_useful, "unit": "TFLOP/s",
                 "frac": achieved / peak_useful, "traffic": None,
-                "kernel": "cc_gemm_split3_tc", "peak_basis": f"{pk['source']} sustained BF16 / 6 products",
+                "kernel": "cc_gemm_split3_tc" if args.prec != "fp64" else "cc_gemm_f64_dmma",
+                "peak_basis": basis,
                 "kernel_share_of_step": gemm_ms_step / ms,
                 "kernel_launches_per_step": gemm_n / args.steps,
                 "padded_flops_per_step": gemm_fl / args.steps}
@@ -317,7 +333,7 @@ def run_ours(args):
         f0.record(stream)
         for k in host:
             dev_in[k].copy_(host[k], non_blocking=True)
-        lad.cc_ladder_step([sd2], prec="mixed", ws=ws, omega=om, D=D, E=E, stream=stream)
+        lad.cc_ladder_step([sd2], prec=args.prec, ws=ws, omega=om, D=D, E=E, stream=stream)
         h_om.copy_(om[0], non_blocking=True)
         h_D.copy_(D[0], non_blocking=True)
         h_E.copy_(E, non_blocking=True)
@@ -330,6 +346,26 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "ms": e2e_ms}
         del host, h_om, h_D, dev_in, sd2
         extra["E"] = g_E
+        # the other split precision on the same system: one step, sampled parity
+        alt = "fp16x2" if args.prec == "mixed" else ("mixed" if args.prec == "fp16x2" else None)
+        if alt is not None:
+            del ws
+            torch.cuda.empty_cache()
+            ws = lad.workspace([sd], alt)
+            lad.cc_ladder_step([sd], prec=alt, ws=ws, omega=om, D=D, E=E, stream=stream)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            lad.cc_ladder_step([sd], prec=alt, ws=ws, omega=om, D=D, E=E, stream=stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            a_ms = a0.elapsed_time(a1)
+            extra["other_precision"] = {
+                "prec": alt, "dtype": PREC[alt][1], "ms_per_step": a_ms, "value": F / (a_ms * 1e-3) / 1e12,
+                "unit": "TFLOP/s", "status": lad.cc_ladder_status(ws),
+                "rel_err_omega_sampled": rel(om[0][:, :, rows, :][:, :, :, cols].cpu().numpy(), o_om),
+                "rel_err_D_sampled": rel(D[0][:, rows, :][:, :, cols].cpu().numpy(), o_D),
+                "E": float(E[0]), "rel_diff_E_vs_timed": abs(float(E[0]) - g_E) / abs(g_E)}
         if not args.no_small:
             del ws
             torch.cuda.empty_cache()
@@ -339,7 +375,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3 split (FP32 accumulate, FP64 reductions)",
+            "vs_baseline": None, "dtype": PREC[args.prec][1],
             "data": "synthetic (seeded, device generator; recipe in DESIGN.md)",
             "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "global_batch": world,
                        "parallelism": f"independent systems, one per GPU ({world})",
@@ -373,8 +409,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     F = sum(counted_flops(o, v, nj) for o, v, nj in sizes)
-    tuned = autotune.tune(systems, prec="mixed", reps=1) if args.autotune else {"block": 0, "win": 0, "source": "default"}
-    ws = lad.workspace(systems, "mixed")
+    tuned = autotune.tune(systems, prec=args.prec, reps=1) if args.autotune else {"block": 0, "win": 0, "source": "default"}
+    ws = lad.workspace(systems, args.prec)
     om = [torch.empty_like(s.t2) for s in systems]
     D = [torch.empty_like(s.L_vv) for s in systems]
     E = torch.empty(len(systems), dtype=torch.float64, device="cuda")
@@ -382,7 +418,7 @@ def run_batch(args):
 
     def one_by_one():
         for k, sd in enumerate(systems):
-            lad.cc_ladder_step([sd], prec="mixed", ws=ws, omega=[om[k]], D=[D[k]], E=E[k:k + 1], stream=stream)
+            lad.cc_ladder_step([sd], prec=args.prec, ws=ws, omega=[om[k]], D=[D[k]], E=E[k:k + 1], stream=stream)
 
     def timed(fn):
         for _ in range(args.warmup):
@@ -400,7 +436,7 @@ def run_batch(args):
     ref = [x.clone() for x in om[:2]]
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        lad.cc_ladder_step(systems, prec="mixed", ws=ws, omega=om, D=D, E=E)
+        lad.cc_ladder_step(systems, prec=args.prec, ws=ws, omega=om, D=D, E=E)
     n0 = lad.cc_ladder_launch_count()
     with Clocks(0) as clk:
         ms_graph = timed(g.replay)
@@ -428,6 +464,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp16x2", "fp64"],
+                    help="arithmetic of the timed path (mixed = 3-piece split-BF16)")
     ap.add_argument("--workload", default="retinal", choices=sorted(WORKLOADS) + ["batch24"])
     ap.add_argument("--autotune", action="store_true", help="batch24: pick tuning knobs with the autotuner")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, oracle sample and small-config legs")

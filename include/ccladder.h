@@ -52,9 +52,13 @@ extern "C" {
 
 typedef enum {
   CC_PREC_FP64 = 0,   /* FP64 operands, FP64 DMMA tensor-core products          */
-  CC_PREC_MIXED = 1   /* 3-piece split-BF16 operands, 6 tcgen05 products per
-                         useful product, FP32 accumulation in TMEM per K-chunk,
-                         FP64 accumulation across chunks and FP64 reductions   */
+  CC_PREC_MIXED = 1,  /* 3-piece split-BF16 operands (24 bits), 6 tcgen05 products
+                         per useful product, FP32 tensor-core accumulation in
+                         restarted windows summed error-free, float-float
+                         intermediates, FP64 outputs and reductions            */
+  CC_PREC_FP16X2 = 2  /* as CC_PREC_MIXED with 2-piece split-FP16 operands
+                         (22 bits) scaled per matrix by a power of two, 3
+                         products per useful product: half the tensor work     */
 } cc_precision;
 
 enum {
@@ -171,11 +175,12 @@ const char* cc_ladder_strerror(int code);
 /* Tuning knobs, process-wide, for calls made afterwards (0 = default):
  *   block_edge   virtual rows per pair block (multiple of 4, <= 256; default
  *                48).  Sets the scratch size: size workspaces after changing it.
- *   win_kblocks  mixed path only: the leading-piece product is re-started every
- *                win_kblocks * 32 K-terms (1, 2, 4 or 8; default 4).  Smaller
- *                windows lower the truncation bias of the tensor-core FP32
- *                accumulation (about 2e-7 relative at 2 vs 3.5e-7 at 4 for the
- *                retinal-scale system) at some speed.
+ *   win_kblocks  split paths only: the leading-piece product is re-started every
+ *                win_kblocks * 32 K-terms, rounded down to the contraction's
+ *                64-term K step (1, 2, 4 or 8; default 4 for CC_PREC_MIXED, 2 for
+ *                CC_PREC_FP16X2).  Smaller windows lower the truncation bias of
+ *                the tensor-core FP32 accumulation (retinal-scale system, split
+ *                BF16: about 1.8e-7 relative at 2 vs 2.6e-7 at 4) at some speed.
  * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
  * on other host threads. */
 int cc_ladder_set_tuning(int block_edge, int win_kblocks);

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ccladder.h"
@@ -34,16 +35,16 @@ void count_launch(int n) { g_launches += n; }
 
 // Process-wide tuning (cc_ladder_set_tuning); 0 = default.
 static std::atomic<int> g_tune_block{0}, g_tune_win{0};
-int tuned_win_kb() {
+int tuned_win_kb(int dflt) {
   const int w = g_tune_win.load();
   if (w > 0) return w;
   const char* e = std::getenv("CC_WIN_KB");
-  return (e && *e) ? std::max(1, std::atoi(e)) : 4;
+  return (e && *e) ? std::max(1, std::atoi(e)) : dflt;
 }
 
 static std::mutex g_err_mu;
 static std::string g_err_text;
-static void note_cuda(cudaError_t e) {
+void note_cuda(cudaError_t e) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   g_err_text = cudaGetErrorString(e);
 }
@@ -81,8 +82,9 @@ __device__ __forceinline__ void pb_pair(int64_t pr, int nb, int diag, int& al, i
 // (trans: read L^J_ca instead, for the adjoint ladder)
 template <typename T>
 __global__ void k_prep_LT(const double* __restrict__ L, int nj, int64_t v2, int v, int trans, T* __restrict__ LT,
-                          int64_t Kj, int64_t piece) {
+                          int64_t Kj, int64_t piece, const float* __restrict__ scl) {
   __shared__ double tile[32][33];
+  const float sc = ld_scale(scl);
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
   const int j0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
@@ -95,13 +97,15 @@ __global__ void k_prep_LT(const double* __restrict__ L, int nj, int64_t v2, int 
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int64_t r = r0 + i;
     const int J = j0 + threadIdx.x;
-    if (r < v2 && J < Kj) Store<T>::put(LT, r * Kj + J, piece, tile[threadIdx.x][i]);
+    if (r < v2 && J < Kj) Store<T>::put(LT, r * Kj + J, piece, tile[threadIdx.x][i], sc);
   }
 }
 
 // L^J_yd -> LN[J][y*vp + d] (zero for d >= v)
 template <typename T>
-__global__ void k_prep_LN(const double* __restrict__ L, int nj, int v, int vp, T* __restrict__ LN, int64_t piece) {
+__global__ void k_prep_LN(const double* __restrict__ L, int nj, int v, int vp, T* __restrict__ LN, int64_t piece,
+                          const float* __restrict__ scl) {
+  const float sc = ld_scale(scl);
   const int64_t total = static_cast<int64_t>(nj) * v * vp;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -109,7 +113,7 @@ __global__ void k_prep_LN(const double* __restrict__ L, int nj, int v, int vp, T
     const int64_t rem = idx - J * v * vp;
     const int y = static_cast<int>(rem / vp), d = static_cast<int>(rem % vp);
     const double x = d < v ? L[(J * v + y) * v + d] : 0.0;
-    Store<T>::put(LN, idx, piece, x);
+    Store<T>::put(LN, idx, piece, x, sc);
   }
 }
 
@@ -119,7 +123,8 @@ __global__ void k_prep_LN(const double* __restrict__ L, int nj, int v, int vp, T
 template <typename T>
 __global__ void k_pack_tau(const double* __restrict__ t1, const double* __restrict__ t2, int o, int v,
                            T* __restrict__ tp, int64_t ldp, int64_t ppiece, T* __restrict__ tm, int64_t ldm,
-                           int64_t mpiece, int minus) {
+                           int64_t mpiece, int minus, const float* __restrict__ scl) {
+  const float sc = ld_scale(scl);
   const int c = blockIdx.x;
   const int64_t pidx = blockIdx.y;
   int i, j;
@@ -135,8 +140,8 @@ __global__ void k_pack_tau(const double* __restrict__ t1, const double* __restri
   for (int d = c + threadIdx.x; d < v; d += blockDim.x) {
     const double a = tij[d] + (t1 ? t1ic * t1[static_cast<int64_t>(j) * v + d] : 0.0);  // tau_ij^cd
     const double b = tji[d] + (t1 ? t1jc * t1[static_cast<int64_t>(i) * v + d] : 0.0);  // tau_ji^cd
-    Store<T>::put(tp, pidx * ldp + kp0 + d, ppiece, a + b);
-    if (minus && pm >= 0 && d > c) Store<T>::put(tm, pm * ldm + km0 + d, mpiece, a - b);
+    Store<T>::put(tp, pidx * ldp + kp0 + d, ppiece, a + b, sc);
+    if (minus && pm >= 0 && d > c) Store<T>::put(tm, pm * ldm + km0 + d, mpiece, a - b, sc);
   }
 }
 
@@ -167,7 +172,8 @@ __global__ void k_transpose(const T* __restrict__ in, int64_t R, int64_t C, int6
 template <typename T>
 __global__ void k_pack_tbar(const double* __restrict__ tb2, int o, int v, int a0, int b0, int nb, int diag,
                             int64_t pair_off, T* __restrict__ bp, int64_t ldp, int64_t ppiece, T* __restrict__ bm,
-                            int64_t ldm, int64_t mpiece, int minus) {
+                            int64_t ldm, int64_t mpiece, int minus, const float* __restrict__ scl) {
+  const float sc = ld_scale(scl);
   int al, bl;
   pb_pair(blockIdx.x, nb, diag, al, bl);
   const int a = a0 + al, b = b0 + bl;
@@ -178,9 +184,9 @@ __global__ void k_pack_tbar(const double* __restrict__ tb2, int o, int v, int a0
       const double x = tb2[(static_cast<int64_t>(i) * o + j) * vv + static_cast<int64_t>(a) * v + b];
       const double y = tb2[(static_cast<int64_t>(j) * o + i) * vv + static_cast<int64_t>(a) * v + b];
       const double w = (i == j) ? 0.25 : 0.5;
-      Store<T>::put(bp, row * ldp + pair_sym(i, j, o), ppiece, w * (x + y));
+      Store<T>::put(bp, row * ldp + pair_sym(i, j, o), ppiece, w * (x + y), sc);
       if (minus && i < j)
-        Store<T>::put(bm, row * ldm + pair_strict(i, j, o), mpiece, (a == b) ? 0.0 : 0.5 * (x - y));
+        Store<T>::put(bm, row * ldm + pair_strict(i, j, o), mpiece, (a == b) ? 0.0 : 0.5 * (x - y), sc);
     }
   }
 }
@@ -201,7 +207,8 @@ __device__ __forceinline__ void tile_pair(int idx, int nt, int& ct, int& dt) {
 template <typename T, typename S>
 __global__ void k_pack_g(const S* __restrict__ G, int64_t ldG, int v, int a0, int b0, int nb, int diag, int nt,
                          T* __restrict__ gp, int64_t ldp, int64_t ppiece, T* __restrict__ gm, int64_t ldm,
-                         int64_t mpiece, int minus) {
+                         int64_t mpiece, int minus, const float* __restrict__ scl) {
+  const float sc = ld_scale(scl);
   using A = Ar<S>;
   using V = typename A::V;
   __shared__ V s1[32][33];  // s1[dd][cc] = G^{ab}_{c,d}
@@ -227,9 +234,9 @@ __global__ void k_pack_g(const S* __restrict__ G, int64_t ldG, int v, int a0, in
     const int c = c0 + r, d = d0 + tx;
     if (c >= v || d >= v || d < c) continue;
     const V gcd = s1[tx][r], gdc = s2[r][tx];
-    Put<T, V>::put(gp, pr * ldp + pair_sym(c, d, v), ppiece, (c == d) ? gcd : A::add(gcd, gdc));
+    Put<T, V>::put(gp, pr * ldp + pair_sym(c, d, v), ppiece, (c == d) ? gcd : A::add(gcd, gdc), sc);
     if (minus && c < d)
-      Put<T, V>::put(gm, pr * ldm + pair_strict(c, d, v), mpiece, same ? A::zero() : A::sub(gcd, gdc));
+      Put<T, V>::put(gm, pr * ldm + pair_strict(c, d, v), mpiece, same ? A::zero() : A::sub(gcd, gdc), sc);
   }
 }
 
@@ -297,7 +304,8 @@ template <typename T, typename S>
 __global__ void k_unpack_gamma(const S* __restrict__ Gp, const S* __restrict__ Gm, int64_t ldp, int64_t ldm,
                                int v, int vp, int a0, int b0, int nb, int diag, int nt, int minus,
                                T* __restrict__ top, int64_t ldt, int64_t tpiece, T* __restrict__ bot, int64_t ldb,
-                               int64_t bpiece) {
+                               int64_t bpiece, const float* __restrict__ scl) {
+  const float sc = ld_scale(scl);
   using A = Ar<S>;
   using V = typename A::V;
   __shared__ V sP[32][33], sM[32][33];  // [c - c0][d - d0], c <= d
@@ -343,7 +351,7 @@ __global__ void k_unpack_gamma(const S* __restrict__ Gp, const S* __restrict__ G
         // sign of M: +1 above the diagonal for (a, b), flipped below it and for (b, a)
         const bool addM = (row < col) == (which == 0);
         const V val = (row == col) ? P : (addM ? A::add(P, M) : A::sub(P, M));
-        Put<T, V>::put(dst, (xrow + row) * ld + ycol + col, piece, val);
+        Put<T, V>::put(dst, (xrow + row) * ld + ycol + col, piece, val, sc);
       }
     }
   }
@@ -405,6 +413,104 @@ __global__ void k_debug_wait(const int* flag, unsigned long long timeout_ns, Sta
 }
 
 // ---------------------------------------------------------------------------
+// operand scales of the FP16 two-piece path
+// ---------------------------------------------------------------------------
+// Bounds are accumulated as float bit patterns with atomicMax (non-negative
+// floats order like their bits) from power-of-two upper bounds of |x| read
+// off the exponent field, so no FP64 arithmetic is needed:
+//   bnd[0] max |L|,    bnd[1] max_(a,c) sum_J (L^J_ac)^2
+//   bnd[2] max |tau|,  bnd[3] max_(c,d) sum_ij (tau_ij^cd)^2
+//   bnd[4] max |tbar|, bnd[5] max_(a,b) sum_ij (tbar_ij^ab)^2
+// Loose bounds only cost a few bits of head-room below FP16's range top;
+// what matters is that no scaled operand can overflow.
+__device__ __forceinline__ float pow2_above(double x) {
+  const int e = static_cast<int>((static_cast<unsigned>(__double2hiint(x)) >> 20) & 0x7FF) - 1023;
+  const int f = min(max(e + 1, -126), 127);  // |x| < 2^(e+1)
+  return __int_as_float((f + 127) << 23);
+}
+
+__device__ __forceinline__ void block_max2(float a, float b, unsigned* pa, unsigned* pb) {
+  __shared__ float ra[32], rb[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a = fmaxf(a, __shfl_down_sync(0xffffffffu, a, off));
+    b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, off));
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    ra[w] = a;
+    rb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < static_cast<int>((blockDim.x + 31) >> 5); ++k) {
+      a = fmaxf(a, ra[k]);
+      b = fmaxf(b, rb[k]);
+    }
+    atomicMax(pa, __float_as_uint(a));
+    atomicMax(pb, __float_as_uint(b));
+  }
+}
+
+// L [nj][v2]: threads over (a,c), loop over J
+__global__ void k_bound_L(const double* __restrict__ L, int nj, int64_t v2, unsigned* __restrict__ bnd) {
+  float mx = 0.f, mrow = 0.f;
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < v2;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float sq = 0.f;
+    for (int J = 0; J < nj; ++J) {
+      const float u = pow2_above(L[static_cast<int64_t>(J) * v2 + r]);
+      sq += u * u;
+      mx = fmaxf(mx, u);
+    }
+    mrow = fmaxf(mrow, sq);
+  }
+  block_max2(mx, mrow, bnd + 0, bnd + 1);
+}
+
+// x_ij^ab = t2[i][j][a][b] + t1[i][a] t1[j][b] (t1 may be null): threads over (a,b)
+__global__ void k_bound_amp(const double* __restrict__ t1, const double* __restrict__ t2, int o, int v,
+                            unsigned* __restrict__ bnd) {
+  const int64_t vv = static_cast<int64_t>(v) * v;
+  float mx = 0.f, mrow = 0.f;
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < vv;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int a = static_cast<int>(r / v), b = static_cast<int>(r % v);
+    float sq = 0.f;
+    for (int i = 0; i < o; ++i)
+      for (int j = 0; j < o; ++j) {
+        float u = pow2_above(t2[(static_cast<int64_t>(i) * o + j) * vv + r]);
+        if (t1) u += pow2_above(t1[static_cast<int64_t>(i) * v + a]) * pow2_above(t1[static_cast<int64_t>(j) * v + b]);
+        sq += u * u;
+        mx = fmaxf(mx, u);
+      }
+    mrow = fmaxf(mrow, sq);
+  }
+  block_max2(mx, mrow, bnd + 0, bnd + 1);
+}
+
+// scale = largest power of two with bound * scale <= 2^14
+__device__ __forceinline__ float pow2_scale(float bound) {
+  if (!(bound > 0.f)) return 1.f;
+  int e;
+  frexpf(16384.f / (bound * 1.01f), &e);  // 16384/bound in [2^(e-1), 2^e)
+  e = min(max(e - 1, -120), 120);
+  return ldexpf(1.f, e);
+}
+
+// sc[0] L (LT, LN), sc[1] tau^pm, sc[2] tbar^pm, sc[3] g^pm, sc[4] Gamma slabs
+__global__ void k_scales(const unsigned* __restrict__ bnd, float* __restrict__ sc) {
+  const float bL = __uint_as_float(bnd[0]), bLrow = __uint_as_float(bnd[1]);
+  const float bt = __uint_as_float(bnd[2]), btrow = __uint_as_float(bnd[3]);
+  const float bb = __uint_as_float(bnd[4]), bbrow = __uint_as_float(bnd[5]);
+  sc[0] = pow2_scale(bL);
+  sc[1] = pow2_scale(2.f * bt);                          // tau_ij + tau_ji
+  sc[2] = pow2_scale(bb);                                // (1/4, 1/2) weighted sums of two
+  sc[3] = pow2_scale(2.f * bLrow);                       // |g+-| <= 2 max |G| <= 2 max_row |L|^2
+  sc[4] = pow2_scale(sqrtf(bbrow) * sqrtf(btrow));       // |Gamma| <= |tbar_ab| |tau_cd|
+}
+
+// ---------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------
 struct PBlock {
@@ -421,7 +527,7 @@ struct Plan {
   std::vector<PBlock> pbs;
   int64_t maxpairs = 0, maxrows = 0, ldO = 0, ldt = 0;
   int64_t n_epart = 0;
-  // byte offsets into the workspace; SIZE_MAX = not present
+  // byte offsets into the workspace; 0 = not present (offset 0 is the status header)
   size_t o_LT = 0, o_LN = 0, o_tp = 0, o_tm = 0, o_tpT = 0, o_tmT = 0, o_bp = 0, o_bm = 0;
   size_t o_G = 0, o_gp = 0, o_gm = 0, o_Op = 0, o_Om = 0, o_Gp = 0, o_Gm = 0, o_Gt = 0, o_Gb = 0, o_E = 0;
   size_t o_D = 0;
@@ -438,7 +544,7 @@ static int env_int(const char* name, int dflt) {
 
 // bytes of an R x C matrix in the path's element format
 static size_t mat_bytes(int prec, int64_t R, int64_t C) {
-  return static_cast<size_t>(R) * static_cast<size_t>(C) * (prec == CC_PREC_MIXED ? 6 : 8);
+  return static_cast<size_t>(R) * static_cast<size_t>(C) * (prec == CC_PREC_MIXED ? 6 : prec == CC_PREC_FP16X2 ? 4 : 8);
 }
 
 static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) {
@@ -508,7 +614,7 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
     P.o_Gm = take(static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
     P.o_Gt = take(mat_bytes(pr, P.maxrows, P.ldt));
     P.o_Gb = take(mat_bytes(pr, P.maxrows, P.ldt));
-    if (prec == CC_PREC_MIXED) P.o_D = take(static_cast<size_t>(nj) * v * v * 8);
+    if (prec != CC_PREC_FP64) P.o_D = take(static_cast<size_t>(nj) * v * v * 8);  // float-float D
   }
   P.o_E = take(static_cast<size_t>(P.n_epart) * 8);
   P.total = cur;
@@ -598,6 +704,12 @@ struct Path<__nv_bfloat16> {
   static constexpr int NP = 3;
   static constexpr bool mixed = true;
 };
+template <>
+struct Path<__half> {
+  using S = float2;
+  static constexpr int NP = 2;
+  static constexpr bool mixed = true;
+};
 
 template <typename T>
 static T* at(char* ws, size_t off) {
@@ -612,6 +724,8 @@ struct Gm {
   int64_t M, N, K;
   void* out; int64_t ldo;
   bool acc;
+  const float* sa = nullptr;  // operand scales (FP16 two-piece path)
+  const float* sb = nullptr;
 };
 
 // K chunk for the FP64 path: whole K unless the launch would have fewer
@@ -636,7 +750,12 @@ static void run_gemms(const Gm* g, int n, Ctx& c) {
     o.status = c.status; o.timeout_ns = c.timeout_ns;
   }
   if (Path<T>::mixed) {
-    for (int i = 0; i < n; ++i) ops[i].mode = g[i].acc ? OUT_FF_ACCUM : OUT_FF_STORE;
+    for (int i = 0; i < n; ++i) {
+      ops[i].mode = g[i].acc ? OUT_FF_ACCUM : OUT_FF_STORE;
+      ops[i].pieces = Path<T>::NP;
+      ops[i].scale_a = g[i].sa;
+      ops[i].scale_b = g[i].sb;
+    }
     c.check(profiled(ops[0], c.st, [&] { return gemm_mixed(ops.data(), n, c.st); }, n > 1 ? &ops[1] : nullptr));
   } else {
     for (int i = 0; i < n; ++i) {
@@ -663,12 +782,33 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
   T* tm = at<T>(ws, P.o_tm);
   const int64_t tp_piece = P.Pop * P.Kvp, tm_piece = P.Pom * P.Kvm;
 
+  // --- operand scales of the FP16 two-piece path (device-side, no host sync)
+  constexpr bool scaled = std::is_same<T, __half>::value;
+  unsigned* bnd = reinterpret_cast<unsigned*>(ws + 64);
+  float* scl = reinterpret_cast<float*>(ws + 128);
+  auto SC = [&](int i) -> const float* { return scaled ? scl + i : nullptr; };
+  if (scaled) {
+    const double* amp = c.adjoint ? sy.tbar2 : sy.t2;
+    c.cuda(cudaMemsetAsync(bnd, 0, 8 * sizeof(unsigned), st));
+    k_bound_L<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(sy.L_vv, nj, vv, bnd);
+    k_bound_amp<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(
+        c.adjoint ? nullptr : sy.t1, amp, o, v, bnd + 2);
+    c.launched(2);
+    if (do_den) {
+      k_bound_amp<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(
+          nullptr, sy.tbar2, o, v, bnd + 4);
+      c.launched();
+    }
+    k_scales<<<1, 1, 0, st>>>(bnd, scl);
+    c.launched();
+  }
+
   // --- tau^pm (both directions need it)
   c.cuda(cudaMemsetAsync(tp, 0, mat_bytes(P.prec, P.Pop, P.Kvp), st));
   if (minus) c.cuda(cudaMemsetAsync(tm, 0, mat_bytes(P.prec, P.Pom, P.Kvm), st));
   k_pack_tau<T><<<dim3(v, static_cast<unsigned>(P.Pop)), 128, 0, st>>>(
       c.adjoint ? nullptr : sy.t1, c.adjoint ? sy.tbar2 : sy.t2, o, v, tp, P.Kvp, tp_piece, tm, P.Kvm, tm_piece,
-      minus);
+      minus, SC(1));
   c.launched();
 
   double* epart = at<double>(ws, P.o_E);
@@ -686,7 +826,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     Op = at<S>(ws, P.o_Op);
     Om = at<S>(ws, P.o_Om);
     k_prep_LT<T><<<dim3(static_cast<unsigned>((vv + 31) / 32), static_cast<unsigned>(P.Kj / 32)), dim3(32, 8), 0,
-                   st>>>(sy.L_vv, nj, vv, v, c.adjoint ? 1 : 0, LT, P.Kj, LT_piece);
+                   st>>>(sy.L_vv, nj, vv, v, c.adjoint ? 1 : 0, LT, P.Kj, LT_piece, SC(0));
     c.launched();
     c.cuda(cudaMemsetAsync(gp, 0, mat_bytes(P.prec, P.maxpairs, P.Kvp), st));
     if (minus) c.cuda(cudaMemsetAsync(gm, 0, mat_bytes(P.prec, P.maxpairs, P.Kvm), st));
@@ -712,7 +852,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     // D accumulates over pair blocks: in float-float scratch (mixed) or
     // directly in the FP64 output (FP64 path)
     Dacc = Path<T>::mixed ? at<S>(ws, P.o_D) : reinterpret_cast<S*>(D);
-    k_prep_LN<T><<<2048, 256, 0, st>>>(sy.L_vv, nj, v, vp, LN, LN_piece);
+    k_prep_LN<T><<<2048, 256, 0, st>>>(sy.L_vv, nj, v, vp, LN, LN_piece, SC(0));
     c.launched();
     c.cuda(cudaMemsetAsync(tpT, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
     k_transpose<T, Path<T>::NP><<<dim3(static_cast<unsigned>((P.Pvp + 31) / 32), static_cast<unsigned>((P.Pop + 31) / 32)),
@@ -729,7 +869,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     for (const PBlock& b : P.pbs) {
       k_pack_tbar<T><<<static_cast<unsigned>(b.npairs), 128, 0, st>>>(sy.tbar2, o, v, b.a0, b.b0, b.nb, b.diag,
                                                                      b.pair_off, bp, P.Kop, bp_piece, bm, P.Kom,
-                                                                     bm_piece, minus);
+                                                                     bm_piece, minus, SC(2));
       c.launched();
     }
     c.cuda(cudaMemsetAsync(Gt, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
@@ -745,17 +885,17 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
       const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
       const Gm g = {LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, LT_piece,
                     LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, LT_piece,
-                    M, N, P.Kj, G, M, false};
+                    M, N, P.Kj, G, M, false, SC(0), SC(0)};
       run_gemms<T>(&g, 1, c);
       k_pack_g<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
-          G, M, v, b.a0, b.b0, b.nb, b.diag, P.nt, gp, P.Kvp, g_piece_p, gm, P.Kvm, g_piece_m, minus);
+          G, M, v, b.a0, b.b0, b.nb, b.diag, P.nt, gp, P.Kvp, g_piece_p, gm, P.Kvm, g_piece_m, minus, SC(3));
       c.launched();
       // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]  (both signs in one launch)
       const Gm lg[2] = {
           {gp, P.Kvp, b.npairs, P.Kvp, g_piece_p, tp, P.Kvp, P.Pop, P.Kvp, tp_piece, b.npairs, P.Pop, P.Kvp, Op,
-           P.ldO, false},
+           P.ldO, false, SC(3), SC(1)},
           {gm, P.Kvm, b.npairs, P.Kvm, g_piece_m, tm, P.Kvm, P.Pom, P.Kvm, tm_piece, b.npairs, P.Pom, P.Kvm, Om,
-           P.ldO, false}};
+           P.ldO, false, SC(3), SC(1)}};
       run_gemms<T>(lg, minus ? 2 : 1, c);
       k_unpack_omega<S><<<static_cast<unsigned>(o2), 256, 0, st>>>(
           Op, Om, P.ldO, o, v, b.a0, b.b0, b.nb, b.diag, b.npairs, minus, omega, sy.tbar2,
@@ -766,13 +906,13 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
       // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]  (both signs in one launch)
       const Gm gg[2] = {
           {tpT, P.Kop, P.Pvp, P.Kop, tpT_piece, bp + b.pair_off * P.Kop, P.Kop, b.npairs, P.Kop, bp_piece, P.Pvp,
-           b.npairs, P.Kop, Gp, P.Kvp, false},
+           b.npairs, P.Kop, Gp, P.Kvp, false, SC(1), SC(2)},
           {tmT, P.Kom, P.Pvm, P.Kom, tmT_piece, bm + b.pair_off * P.Kom, P.Kom, b.npairs, P.Kom, bm_piece, P.Pvm,
-           b.npairs, P.Kom, Gm_, P.Kvm, false}};
+           b.npairs, P.Kom, Gm_, P.Kvm, false, SC(1), SC(2)}};
       run_gemms<T>(gg, minus ? 2 : 1, c);
       k_unpack_gamma<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
           Gp, Gm_, P.Kvp, P.Kvm, v, vp, b.a0, b.b0, b.nb, b.diag, P.nt, minus, Gt, P.ldt, gt_piece, Gb, P.ldt,
-          gt_piece);
+          gt_piece, SC(4));
       c.launched();
       // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd  (top and, off the diagonal, bottom)
       const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 64);
@@ -780,10 +920,10 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
       const Gm dg[2] = {
           {Gt, P.ldt, Mt, P.ldt, gt_piece, LN + static_cast<int64_t>(b.b0) * vp, static_cast<int64_t>(v) * vp, nj,
            static_cast<int64_t>(v - b.b0) * vp, LN_piece, Mt, nj, Kt, Dacc + static_cast<int64_t>(b.a0) * v, vv,
-           true},
+           true, SC(4), SC(0)},
           {Gb, P.ldt, Mb, P.ldt, gt_piece, LN + static_cast<int64_t>(b.a0) * vp, static_cast<int64_t>(v) * vp, nj,
            static_cast<int64_t>(v - b.a0) * vp, LN_piece, Mb, nj, Kb, Dacc + static_cast<int64_t>(b.b0) * v, vv,
-           true}};
+           true, SC(4), SC(0)}};
       run_gemms<T>(dg, b.diag ? 1 : 2, c);
     }
   }
@@ -837,7 +977,7 @@ static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int whic
 static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
                int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream,
                bool adjoint = false) {
-  if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED) return CC_ERR_ARG;
+  if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED && prec != CC_PREC_FP16X2) return CC_ERR_ARG;
   int rc = validate(sys, n_sys, den || want_E || adjoint);
   if (rc) return rc;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
@@ -866,6 +1006,8 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
     double* Ei = want_E ? E + i : nullptr;
     if (prec == CC_PREC_MIXED)
       run_system<__nv_bfloat16>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
+    else if (prec == CC_PREC_FP16X2)
+      run_system<__half>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
     else
       run_system<double>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
   }
@@ -879,7 +1021,9 @@ using namespace ccl;
 extern "C" {
 
 size_t cc_ladder_workspace_size(const cc_ladder_system* sys, int n_sys, cc_precision p, int which) {
-  if (validate(sys, n_sys, false) || (p != CC_PREC_FP64 && p != CC_PREC_MIXED) || !(which & CC_WS_STEP)) return 0;
+  if (validate(sys, n_sys, false) || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) ||
+      !(which & CC_WS_STEP))
+    return 0;
   return ws_need(sys, n_sys, p, which);
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,34 +36,40 @@ __device__ __forceinline__ Split3 split3(double x) {
   return s;
 }
 
-// Element store for the two precisions: FP64 (one piece) or split-BF16
-// (three pieces `piece` elements apart).
+// Element store of an FP64 value for the operand formats: FP64 (one piece),
+// split-BF16 (three pieces `piece` elements apart) or scaled split-FP16 (two
+// pieces of x * scl; scl is a power of two chosen so that |x| * scl <= 2^14).
 template <typename T>
 struct Store;
 
 template <>
 struct Store<double> {
-  static __device__ __forceinline__ void put(double* base, int64_t idx, int64_t /*piece*/, double x) {
+  static __device__ __forceinline__ void put(double* base, int64_t idx, int64_t /*piece*/, double x, float) {
     base[idx] = x;
-  }
-  static __device__ __forceinline__ double get(const double* base, int64_t idx, int64_t /*piece*/) {
-    return base[idx];
   }
 };
 
 template <>
 struct Store<__nv_bfloat16> {
-  static __device__ __forceinline__ void put(__nv_bfloat16* base, int64_t idx, int64_t piece, double x) {
+  static __device__ __forceinline__ void put(__nv_bfloat16* base, int64_t idx, int64_t piece, double x, float) {
     Split3 s = split3(x);
     base[idx] = s.p[0];
     base[idx + piece] = s.p[1];
     base[idx + 2 * piece] = s.p[2];
   }
-  static __device__ __forceinline__ double get(const __nv_bfloat16* base, int64_t idx, int64_t piece) {
-    return (double)__bfloat162float(base[idx]) + (double)__bfloat162float(base[idx + piece]) +
-           (double)__bfloat162float(base[idx + 2 * piece]);
+};
+
+template <>
+struct Store<__half> {
+  static __device__ __forceinline__ void put(__half* base, int64_t idx, int64_t piece, double x, float scl) {
+    const double y = x * static_cast<double>(scl);
+    const __half h0 = __double2half(y);
+    base[idx] = h0;
+    base[idx + piece] = __double2half(y - static_cast<double>(__half2float(h0)));
   }
 };
+
+__device__ __forceinline__ float ld_scale(const float* s) { return s ? *s : 1.f; }
 
 // ---------------------------------------------------------------- float-float
 // Intermediates of the mixed path are unevaluated sums hi + lo of two FP32
@@ -122,21 +129,31 @@ struct Ar<float2> {
   }
 };
 
-// Operand store: FP64 path keeps the value, mixed path splits float-float
-// values into three BF16 pieces.
+// Operand store: FP64 path keeps the value, mixed paths split float-float
+// values into three BF16 pieces or two scaled FP16 pieces.
 template <typename T, typename V>
 struct Put;
 template <>
 struct Put<double, double> {
-  static __device__ __forceinline__ void put(double* base, int64_t idx, int64_t, double x) { base[idx] = x; }
+  static __device__ __forceinline__ void put(double* base, int64_t idx, int64_t, double x, float) { base[idx] = x; }
 };
 template <>
 struct Put<__nv_bfloat16, float2> {
-  static __device__ __forceinline__ void put(__nv_bfloat16* base, int64_t idx, int64_t piece, float2 x) {
+  static __device__ __forceinline__ void put(__nv_bfloat16* base, int64_t idx, int64_t piece, float2 x, float) {
     const Split3 s = split3_ff(x);
     base[idx] = s.p[0];
     base[idx + piece] = s.p[1];
     base[idx + 2 * piece] = s.p[2];
+  }
+};
+// x * scl = h0 + h1 in FP32 arithmetic (scl a power of two: the products are exact)
+template <>
+struct Put<__half, float2> {
+  static __device__ __forceinline__ void put(__half* base, int64_t idx, int64_t piece, float2 x, float scl) {
+    const float hi = x.x * scl;
+    const __half h0 = __float2half_rn(hi);
+    base[idx] = h0;
+    base[idx + piece] = __float2half_rn((hi - __half2float(h0)) + x.y * scl);
   }
 };
 
@@ -365,6 +382,11 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
   d |= (uint64_t)2 << 61;                           // layout: 128-byte swizzle
   return d;
+}
+
+// Instruction descriptor, kind::f16: F16 x F16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.

@@ -6,7 +6,7 @@
 // The output is written transposed (M contiguous) so that a warp's lanes,
 // which hold consecutive rows m of the accumulator, store coalesced.
 //
-// Mixed path (gemm_mixed): split-BF16 operands, one CTA per 128 x 128
+// Mixed paths (gemm_mixed): split operands (3 BF16 or 2 scaled FP16 pieces), one CTA per 128 x 128
 // output tile over the whole K, float-float output (float2 hi/lo) either
 // stored (OUT_FF_STORE) or added to what is there (OUT_FF_ACCUM, a plain
 // read-modify-write: tiles are owned by one CTA).  Up to two problems of
@@ -36,6 +36,9 @@ struct GemmOp {
   int64_t ldo = 0;
   int mode = OUT_F64_STORE;
   int64_t kchunk = 0;           // FP64 path only: K per CTA (0 = whole K)
+  int pieces = 3;               // mixed path: 3 BF16 pieces or 2 scaled FP16 pieces
+  const float* scale_a = nullptr;  // FP16 pieces: device scales of A and B (the output is
+  const float* scale_b = nullptr;  // divided by their product), else null
   Status* status = nullptr;
   uint64_t timeout_ns = 2000000000ull;
 };
@@ -44,10 +47,14 @@ struct GemmOp {
 int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream);
 int gemm_f64(const GemmOp& op, cudaStream_t stream);
 
+// Records the text of a failed CUDA call for cc_ladder_strerror.
+void note_cuda(cudaError_t e);
+
 // Launch counter shared by every kernel launch of the library.
 void count_launch(int n = 1);
 
-// Leading-product window of the mixed contraction, in k-blocks of 32.
-int tuned_win_kb();
+// Leading-product window of the mixed contraction, in k-blocks of 32
+// (the tuning knob if set, else `dflt`).
+int tuned_win_kb(int dflt);
 
 }  // namespace ccl

@@ -1,34 +1,47 @@
-// Split-BF16 tensor-core contraction for sm_103a (tcgen05 + TMA + TMEM).
+// Split-operand tensor-core contraction for sm_103a (tcgen05 + TMA + TMEM).
 //
-// Every operand element is stored as three BF16 pieces x = x0 + x1 + x2
-// (24 significant bits, each piece the round-to-nearest BF16 of what the
-// previous ones left).  One useful product a*b is formed from the six piece
-// products whose weight is at least 2^-16 of the leading one:
-//   a0b0 + (a0b1 + a1b0 + a0b2 + a1b1 + a2b0),
-// the dropped terms are O(2^-24) relative.
+// Two piece schemes share the kernel.
+//  * NP = 3 (split BF16): every operand element is x = x0 + x1 + x2, three
+//    BF16 pieces (24 significant bits, each the round-to-nearest BF16 of what
+//    the previous ones left).  A useful product a*b is formed from the six
+//    piece products of weight at least 2^-16 of the leading one,
+//    a0b0 + (a0b1 + a1b0 + a0b2 + a1b1 + a2b0); the dropped terms are
+//    O(2^-24) relative.
+//  * NP = 2 (scaled split FP16): the operand matrix is first multiplied by a
+//    power of two that brings its largest element to at most 2^14, then
+//    x = x0 + x1 with two FP16 pieces (22 significant bits); a*b is
+//    a0b0 + (a0b1 + a1b0), the dropped a1b1 is O(2^-22) relative.  The
+//    epilogue divides by the two scales (exact).
 //
 // Accumulation.  The tensor core adds each K=16 step into its FP32
 // accumulator with a truncating (round-toward-zero) alignment, which biases
-// every output by about -1.7e-8 per step, growing linearly with K.  So:
+// every output toward zero, growing linearly with the number of steps.  So:
 //   * the leading product a0b0 goes to its own TMEM accumulator H, which is
-//     restarted every 128 K terms by default (tunable), so the bias
-//     never spans more than 8 tensor-core steps; the drain warps add
-//     the window sums in FP32 (round to nearest, unbiased) and every FOLD
-//     windows fold that partial sum error-free into a two-sum (HI in
-//     registers, LO in TMEM);
-//   * the five small products (weight <= 2^-8 of the leading one) go to a
-//     second accumulator L, drained the same way every 4096 terms; its
-//     truncation bias is scaled down by that weight.
-// H is double-buffered (H0, H1) so the drain of one window overlaps the
-// MMAs of the next; the MMA warp waits for the (rare) L drain.  One CTA
-// owns a 128 x 128 output tile over the whole K and writes the float-float
-// result hi + lo (or adds it to the float-float value already there).
+//     restarted every window of K terms (default 128 for BF16 pieces, 64 for
+//     FP16 pieces, whose 22-bit products lose more bits per step; tunable),
+//     so the bias never spans more than a few tensor-core steps;
+//   * the small products (weight <= 2^-8 of the leading one) go to a second
+//     accumulator L, restarted every 4096 terms; its truncation bias is
+//     scaled down by that weight.
+// The drain warps add the window sums (and the L segment sums) in FP32
+// (round to nearest, unbiased) and every FOLD windows fold that partial sum
+// error-free into a two-sum (HI in registers, LO in TMEM), so the long K sum
+// carries no rounding drift.  H is double-buffered (H0, H1) so the drain of
+// one window overlaps the MMAs of the next; the MMA warp waits for the
+// (rare) L drain.  Measured on GB300, the drain is what bounds short windows:
+// a two-sum per window (instead of one FP32 add) or a third H buffer with
+// both halves of the two-sum in registers (96 registers a thread, spilling)
+// ran 10-25% slower.  One CTA owns a 128 x 128 output tile over the whole K
+// and writes the float-float result hi + lo (or adds it to the value there).
 //
 // CTA = 18 warps: warp 0 issues TMA loads (one elected lane), warp 1 owns
 // TMEM and issues tcgen05.mma (one elected lane), warps 2-17 drain (warp w
-// reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile 128 x 128 x 64,
-// 2-stage smem ring (96 KB per stage: 3 A pieces + 3 B pieces, 128-byte
-// swizzle: 128-byte TMA rows move operands ~1.2x faster than 64-byte ones).  TMEM columns: H0 [0,128), H1 [128,256), L [256,384), lo [384,512).
+// reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile
+// 128 x 128 x 64 with a 192 KB smem ring (BF16: 2 stages of 3 A + 3 B
+// pieces; FP16: 3 stages of 2 + 2), 128-byte swizzle (128-byte TMA rows move
+// operands ~1.2x faster than 64-byte ones).  Clusters of CLUSTER CTAs take
+// adjacent n-tiles of one m-tile and multicast its A tile.  TMEM columns:
+// H0 [0,128), H1 [128,256), L [256,384), LO [384,512).
 // Every wait is bounded (globaltimer) and latches CC_ERR_TIMEOUT.
 #include <cudaTypedefs.h>
 
@@ -43,30 +56,62 @@
 namespace ccl {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, NP = 3;
+constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int RASTER_GROUP = 8;           // m-tiles per raster group (L2 reuse of B panels)
 #ifndef CC_GEMM_CLUSTER
 #define CC_GEMM_CLUSTER 2
 #endif
 constexpr int CLUSTER = CC_GEMM_CLUSTER;  // CTAs sharing one A tile (TMA multicast); 1 or 2
-constexpr int FOLD = 8;                   // H windows summed in FP32 before the error-free fold
-constexpr int A_PIECE = BM * BK * 2;      // 16384 B
+constexpr int A_PIECE = BM * BK * 2;      // 16384 B (one 16-bit piece of a 128 x 64 tile)
 constexpr int A_HALF = A_PIECE / CLUSTER; // bytes of one piece's row slice
 constexpr int B_PIECE = BN * BK * 2;      // 16384 B
-constexpr int A_STAGE = NP * A_PIECE;     // 49152 B
-constexpr int B_STAGE = NP * B_PIECE;     // 49152 B
-constexpr int STAGE = A_STAGE + B_STAGE;  // 98304 B
-constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256;
+constexpr int SMEM_BYTES = 196608 + 1024 + 256;  // stages * stage bytes is 192 KB for both schemes
 constexpr uint32_t TMEM_COLS = 512;
+constexpr int FOLD = 8;                   // H windows summed in FP32 before the error-free fold
 constexpr uint32_t COL_H0 = 0, COL_H1 = 128, COL_L = 256, COL_LO = 384;
 constexpr int NDRAIN = 16;                // draining warps (4 per TMEM lane quarter)
 constexpr int NTHREADS = (2 + NDRAIN) * 32;
 constexpr int DCOLS = BN / (NDRAIN / 4);  // accumulator columns per drain thread
-constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+
+// Piece schemes.  NP = 3: BF16 pieces, six products, the leading one last.
+// NP = 2: FP16 pieces of power-of-two scaled operands, three products.
+template <int NP>
+struct Scheme;
+template <>
+struct Scheme<3> {
+  static constexpr int STAGES = 2;
+  static constexpr int NPROD = 6;
+  static constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+  static __device__ __forceinline__ void pieces(int q, int& pa, int& pb) {
+    switch (q) {
+      case 0: pa = 2; pb = 0; break;
+      case 1: pa = 1; pb = 1; break;
+      case 2: pa = 0; pb = 2; break;
+      case 3: pa = 1; pb = 0; break;
+      case 4: pa = 0; pb = 1; break;
+      default: pa = 0; pb = 0; break;
+    }
+  }
+};
+template <>
+struct Scheme<2> {
+  static constexpr int STAGES = 3;
+  static constexpr int NPROD = 3;
+  static constexpr uint32_t IDESC = idesc_f16_f32(BM, BN);
+  static __device__ __forceinline__ void pieces(int q, int& pa, int& pb) {
+    switch (q) {
+      case 0: pa = 1; pb = 0; break;
+      case 1: pa = 0; pb = 1; break;
+      default: pa = 0; pb = 0; break;
+    }
+  }
+};
 
 struct Prob {
-  CUtensorMap ta, tb;  // ta: A box {32, 128/CLUSTER, 1} (one piece, one row slice); tb: B box {32, 128, 3}
+  CUtensorMap ta, tb;  // ta: A box {64, 128/CLUSTER, 1} (one piece, one row slice); tb: B box {64, 128, NP}
   float2* out;
+  const float* sa;     // operand scales (mixed FP16 scheme) or null
+  const float* sb;
   long long ldo;
   int M, N, K, mode;
 };
@@ -75,18 +120,6 @@ struct Probs {
   int win_kb;  // k-blocks per H window
   int lwin;    // H windows per L segment
 };
-
-// piece indices of the six kept products; q = 5 is the leading a0b0
-__device__ __forceinline__ void product_pieces(int q, int& pa, int& pb) {
-  switch (q) {
-    case 0: pa = 2; pb = 0; break;
-    case 1: pa = 1; pb = 1; break;
-    case 2: pa = 0; pb = 2; break;
-    case 3: pa = 1; pb = 0; break;
-    case 4: pa = 0; pb = 1; break;
-    default: pa = 0; pb = 0; break;
-  }
-}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -136,8 +169,12 @@ __device__ __forceinline__ void fold_cols(uint32_t lo_addr, float (&acc)[DCOLS],
   tmem_st_wait();
 }
 
+template <int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     cc_gemm_split3_tc(const __grid_constant__ Probs P, Status* st, unsigned long long timeout_ns) {
+  using SC = Scheme<NP>;
+  constexpr int STAGES = SC::STAGES;
+  constexpr int A_STAGE = NP * A_PIECE, B_STAGE = NP * B_PIECE, STAGE = A_STAGE + B_STAGE;
   const Prob& pr = P.p[blockIdx.z];
   const int WIN_KB = P.win_kb, LWIN = P.lwin;
   // grouped raster: consecutive CTAs sweep the n-tiles of RASTER_GROUP m-tiles
@@ -249,15 +286,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int ks = 0; ks < BK / 16; ++ks) {
             const bool first = (kb == kb_beg) && ks == 0;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
+            for (int q = 0; q < SC::NPROD; ++q) {
               int pa, pb;
-              product_pieces(q, pa, pb);
+              SC::pieces(q, pa, pb);
               const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
               const uint64_t bd = sdesc_k_sw128(b_base + pb * B_PIECE + ks * 32);
-              if (q == 5)
-                umma_f16(tmem + hcol, ad, bd, IDESC, first ? 0u : 1u);
+              if (q == SC::NPROD - 1)
+                umma_f16(tmem + hcol, ad, bd, SC::IDESC, first ? 0u : 1u);
               else
-                umma_f16(tmem + COL_L, ad, bd, IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
+                umma_f16(tmem + COL_L, ad, bd, SC::IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
             }
           }
           umma_commit_mc(&empty[s], cmask);  // releases the stage in every CTA it was written to
@@ -318,6 +355,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0) latch_error(st, kErrTimeout, 103);
     } else {
       const int row = m0 + q * 32 + lane;
+      const float inv = (1.f / ld_scale(pr.sa)) * (1.f / ld_scale(pr.sb));  // powers of two: exact
 #pragma unroll
       for (int c = 0; c < DCOLS; c += 8) {
         uint32_t l[8];
@@ -331,7 +369,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int j = 0; j < 8; ++j) {
             const int n = n0 + cb + c + j;
             if (n < pr.N) {
-              float2 v = ff_fast_two_sum(HI[c + j], __uint_as_float(l[j]));
+              float2 v = ff_scale(ff_fast_two_sum(HI[c + j], __uint_as_float(l[j])), inv);
               float2* p = pr.out + static_cast<long long>(n) * pr.ldo + row;
               if (pr.mode == OUT_FF_ACCUM) v = ff_add(*p, v);
               *p = v;
@@ -369,40 +407,43 @@ EncodeFn get_encode() {
 
 // 3-D map over the piece-stacked BF16 matrix: dims {cols, rows, 3 pieces}.
 bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int64_t piece,
-              int box_rows, int box_pieces = 3) {
+              int box_rows, int box_pieces, int npieces, CUtensorMapDataType dtype) {
   EncodeFn enc = get_encode();
   if (!enc) return false;
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows), 3};
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(npieces)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(piece) * 2};
   cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows),
                        static_cast<cuuint32_t>(box_pieces)};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, dtype, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
-  if (nops < 1 || nops > 2) return -1;
+template <int NP>
+int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   Probs P;
   memset(&P, 0, sizeof(P));
+  const CUtensorMapDataType dt = NP == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   int64_t tiles = 0;
-  P.win_kb = std::max(1, tuned_win_kb() * 32 / BK);  // window given in 32-term units
+  // window given in 32-term units; FP16 leading products (22 significant
+  // bits) lose more to the truncating accumulation than BF16 ones (16 bits),
+  // so their default window is half as long
+  P.win_kb = std::max(1, tuned_win_kb(NP == 2 ? 2 : 4) * 32 / BK);
   P.lwin = std::max(1, (4096 / BK) / P.win_kb);      // L segment of 4096 K terms
   for (int i = 0; i < nops; ++i) {
     const GemmOp& op = ops[i];
     if (op.mode != OUT_FF_STORE && op.mode != OUT_FF_ACCUM) return -1;
     if (op.M <= 0 || op.N <= 0 || op.K <= 0) return -1;
-    if (op.K % BK || op.K > 2147483647LL || op.M > (int64_t)BM * 65535 || op.N > (int64_t)BN * 2147483647LL)
-      return -1;
+    if (op.K % BK || op.K > 2147483647LL || op.M > 2147483647LL || op.N > 2147483647LL) return -1;
     if ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.B)) & 15) return -1;
     if ((op.lda | op.ldb | op.a_piece | op.b_piece) & 7) return -1;
-    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM / CLUSTER, 1)) return -4;
-    if (!make_map(&P.p[i].tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN)) return -4;
+    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM / CLUSTER, 1, NP, dt)) return -4;
+    if (!make_map(&P.p[i].tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN, NP, NP, dt)) return -4;
     P.p[i].out = static_cast<float2*>(op.out);
+    P.p[i].sa = op.scale_a;
+    P.p[i].sb = op.scale_b;
     P.p[i].ldo = op.ldo;
     P.p[i].M = static_cast<int>(op.M);
     P.p[i].N = static_cast<int>(op.N);
@@ -414,9 +455,12 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(cc_gemm_split3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
-  if (attr_err != cudaSuccess) return -4;
+  if (attr_err != cudaSuccess) {
+    note_cuda(attr_err);
+    return -4;
+  }
   if (tiles > 2147483647LL) return -1;
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
@@ -431,9 +475,25 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, cc_gemm_split3_tc, P, ops[0].status, ops[0].timeout_ns) != cudaSuccess) return -4;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, cc_gemm_split3_tc<NP>, P, ops[0].status, ops[0].timeout_ns);
+  if (e == cudaSuccess) e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return -4;
+  }
   count_launch();
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -4;
+  return 0;
+}
+
+}  // namespace
+
+int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
+  if (nops < 1 || nops > 2) return -1;
+  for (int i = 1; i < nops; ++i)
+    if (ops[i].pieces != ops[0].pieces) return -1;
+  if (ops[0].pieces == 3) return launch<3>(ops, nops, stream);
+  if (ops[0].pieces == 2) return launch<2>(ops, nops, stream);
+  return -1;
 }
 
 }  // namespace ccl

@@ -16,7 +16,7 @@ import torch
 
 from . import _build
 
-CC_PREC = {"fp64": 0, "mixed": 1}
+CC_PREC = {"fp64": 0, "mixed": 1, "fp16x2": 2}
 CC_WS_RESIDUAL, CC_WS_DENSITY, CC_WS_LAGRANGIAN, CC_WS_STEP = 1, 2, 4, 7
 
 _lib = None
