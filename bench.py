@@ -42,6 +42,13 @@ PREC = {
 }
 
 
+# DRAM bytes of the contraction kernel per step (sum of dram__bytes_read.sum + dram__bytes_write.sum over its
+# launches of one step) from one-pass ncu captures of this kernel version; null for combinations not captured
+TRAFFIC = {
+    ("retinal", "mixed"): (2.358e13, "profiles/cc_gemm_split3_tc_retinal_o78_v650_nj4000_dram_bytes.md"),
+}
+
+
 def counted_flops(o, v, nj):
     pvp, pvm = v * (v + 1) // 2, v * (v - 1) // 2
     qop, qom = o * (o + 1) // 2, o * (o - 1) // 2
@@ -288,8 +295,11 @@ def run_ours(args):
         # FP16 and BF16 share the dense tensor rate: the measured BF16 figure serves both
         peak_useful = pk["bf16_sustained"] / nprod
         basis = f"{pk['source']} sustained BF16 (= FP16 rate) / {nprod} products"
+    traffic, traffic_src = TRAFFIC.get((args.workload, args.prec), (None, None))
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_useful, "unit": "TFLOP/s",
-                "frac": achieved / peak_useful, "traffic": None,
+                "frac": achieved / peak_useful, "traffic": traffic,
+                "traffic_basis": ("DRAM bytes per step, all contraction launches of one step (ncu, one pass): "
+                                  + traffic_src) if traffic_src else None,
                 "kernel": "cc_gemm_split3_tc" if args.prec != "fp64" else "cc_gemm_f64_dmma",
                 "peak_basis": basis,
                 "kernel_share_of_step": gemm_ms_step / ms,
