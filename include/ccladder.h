@@ -117,6 +117,20 @@ int cc_ladder_density(const cc_ladder_system* sys, int n_sys,
                       double* const* D, cc_precision p,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* Excited-state V^4 density intermediate (App. A: d^es_abcd = O^(2)_abcd(L2, U)
+ * with U = T2 R0 + R2), in the T1-transformed basis:
+ *     D^J_ac = sum_bd Gamma_abcd L^J_bd,  Gamma_abcd = sum_ij L2_ij^ab U_ij^cd,
+ *     U_ij^cd = R0[s] * t2_ij^cd + R2[s]_ij^cd.
+ * sys[s].tbar2 holds the left doubles L2, sys[s].t2 the ground-state doubles
+ * T2 and L_vv the (T1-transformed) Cholesky vectors; sys[s].t1 is not read.
+ * R2[s] is a device [o][o][v][v] buffer (pair symmetric, like t2); R0 is a
+ * HOST array of n_sys doubles.  D[s] as for cc_ladder_density; workspace:
+ * CC_WS_DENSITY. */
+int cc_ladder_density_es(const cc_ladder_system* sys, int n_sys,
+                         const double* const* R2, const double* R0,
+                         double* const* D, cc_precision p,
+                         void* ws, size_t ws_bytes, void* stream);
+
 /* E[s] = sum_ijab tbar_ij^ab Omega_ij^ab (Eq. lagrangian, the ladder slice),
  * an FP64 reduction written to the device array E[n_sys].  If omega_opt is
  * non-NULL its buffers hold Omega already (from cc_ladder_residual); if NULL
@@ -138,6 +152,29 @@ int cc_ladder_step(const cc_ladder_system* sys, int n_sys,
 int cc_ladder_update(const cc_ladder_system* sys, int n_sys,
                      double* const* omega, double* const* t2_out,
                      void* stream);
+
+/* T1-transformed Cholesky vectors, virtual-virtual block (Sec. II.C: the
+ * integrals and Cholesky vectors in the T1-transformed basis, x = I - t1,
+ * y = I + t1^T, L^J -> x L^J y^T):
+ *     L_vv_t1[J][a][c] = L_vv[J][a][c] - sum_i t1[i][a] * L_ov[J][i][c]
+ * In that basis the ladder takes t2 itself: run the calls above with
+ * L_vv = L_vv_t1 and t1 = NULL (the kernels do not assume L^J symmetric).
+ * L_ov [nj][o][v] is the occupied-virtual block of the MO Cholesky vectors,
+ * L^J_ic at (J*o + i)*v + c; t1 [o][v]; L_vv_t1 [nj][v][v], must not overlap
+ * an input.  FP64 throughout.  Device pointers; asynchronous on `stream`. */
+int cc_ladder_t1_transform(int32_t o, int32_t v, int32_t nj, const double* L_vv,
+                           const double* L_ov, const double* t1, double* L_vv_t1,
+                           void* stream);
+
+/* Back-transformation of a three-index density intermediate to the MO
+ * basis (Sec. II.C: (W^J)^MO = x^T W^J y) for a W^J that is non-zero in
+ * the virtual-virtual block only, such as D from cc_ladder_density in the
+ * T1 basis.  The vv block is unchanged; the occupied-virtual block is
+ *     W_ov[J][i][c] = - sum_a t1[i][a] * W_vv[J][a][c]
+ * W_vv [nj][v][v], t1 [o][v], W_ov [nj][o][v] (output, must not overlap an
+ * input).  FP64.  Device pointers; asynchronous on `stream`. */
+int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_vv,
+                              const double* t1, double* W_ov, void* stream);
 
 /* Synchronises `stream`, then returns and clears the device-side status
  * latched in `ws` by earlier calls (CC_OK or CC_ERR_TIMEOUT), or

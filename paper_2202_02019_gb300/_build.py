@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libccladder.so")
-SOURCES = ["ccladder.cu", "gemm_mixed.cu", "gemm_f64.cu", "noalloc.cu"]
+SOURCES = ["ccladder.cu", "gemm_mixed.cu", "gemm_f64.cu", "noalloc.cu", "t1.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{INC}", f"-I{CSRC}"]

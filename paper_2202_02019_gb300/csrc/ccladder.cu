@@ -120,10 +120,13 @@ __global__ void k_prep_LN(const double* __restrict__ L, int nj, int v, int vp, T
 // tau^pm packed, rows = occupied pairs, columns = virtual pairs (K-major for
 // the ladder):  tau+[p+(i,j)][k+(c,d)] = tau_ij^cd + tau_ji^cd   (i<=j, c<=d)
 //               tau-[p-(i,j)][k-(c,d)] = tau_ij^cd - tau_ji^cd   (i<j,  c<d)
+// With r2 non-null the packed doubles are U = r0 t2 + r2 instead (the
+// excited-state C2 of App. A; t1 is then not read).
 template <typename T>
 __global__ void k_pack_tau(const double* __restrict__ t1, const double* __restrict__ t2, int o, int v,
                            T* __restrict__ tp, int64_t ldp, int64_t ppiece, T* __restrict__ tm, int64_t ldm,
-                           int64_t mpiece, int minus, const float* __restrict__ scl) {
+                           int64_t mpiece, int minus, const float* __restrict__ scl,
+                           const double* __restrict__ r2 = nullptr, double r0 = 1.0) {
   const float sc = ld_scale(scl);
   const int c = blockIdx.x;
   const int64_t pidx = blockIdx.y;
@@ -137,9 +140,17 @@ __global__ void k_pack_tau(const double* __restrict__ t1, const double* __restri
   const int64_t kp0 = pair_sym(c, c, v) - c;
   const int64_t km0 = (c + 1 < v) ? pair_strict(c, c + 1, v) - (c + 1) : 0;
   const int64_t pm = (i < j) ? pair_strict(i, j, o) : -1;
+  const double* rij = r2 ? r2 + (tij - t2) : nullptr;
+  const double* rji = r2 ? r2 + (tji - t2) : nullptr;
   for (int d = c + threadIdx.x; d < v; d += blockDim.x) {
-    const double a = tij[d] + (t1 ? t1ic * t1[static_cast<int64_t>(j) * v + d] : 0.0);  // tau_ij^cd
-    const double b = tji[d] + (t1 ? t1jc * t1[static_cast<int64_t>(i) * v + d] : 0.0);  // tau_ji^cd
+    double a, b;
+    if (r2) {
+      a = fma(r0, tij[d], rij[d]);  // U_ij^cd
+      b = fma(r0, tji[d], rji[d]);  // U_ji^cd
+    } else {
+      a = tij[d] + (t1 ? t1ic * t1[static_cast<int64_t>(j) * v + d] : 0.0);  // tau_ij^cd
+      b = tji[d] + (t1 ? t1jc * t1[static_cast<int64_t>(i) * v + d] : 0.0);  // tau_ji^cd
+    }
     Store<T>::put(tp, pidx * ldp + kp0 + d, ppiece, a + b, sc);
     if (minus && pm >= 0 && d > c) Store<T>::put(tm, pm * ldm + km0 + d, mpiece, a - b, sc);
   }
@@ -469,8 +480,10 @@ __global__ void k_bound_L(const double* __restrict__ L, int nj, int64_t v2, unsi
 }
 
 // x_ij^ab = t2[i][j][a][b] + t1[i][a] t1[j][b] (t1 may be null): threads over (a,b)
+// (with r2 non-null: x = r0 t2 + r2, t1 not read)
 __global__ void k_bound_amp(const double* __restrict__ t1, const double* __restrict__ t2, int o, int v,
-                            unsigned* __restrict__ bnd) {
+                            unsigned* __restrict__ bnd, const double* __restrict__ r2 = nullptr, double r0 = 1.0) {
+  const float r0b = pow2_above(r0);
   const int64_t vv = static_cast<int64_t>(v) * v;
   float mx = 0.f, mrow = 0.f;
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < vv;
@@ -479,8 +492,12 @@ __global__ void k_bound_amp(const double* __restrict__ t1, const double* __restr
     float sq = 0.f;
     for (int i = 0; i < o; ++i)
       for (int j = 0; j < o; ++j) {
-        float u = pow2_above(t2[(static_cast<int64_t>(i) * o + j) * vv + r]);
-        if (t1) u += pow2_above(t1[static_cast<int64_t>(i) * v + a]) * pow2_above(t1[static_cast<int64_t>(j) * v + b]);
+        const int64_t e = (static_cast<int64_t>(i) * o + j) * vv + r;
+        float u = pow2_above(t2[e]);
+        if (r2)
+          u = r0b * u + pow2_above(r2[e]);
+        else if (t1)
+          u += pow2_above(t1[static_cast<int64_t>(i) * v + a]) * pow2_above(t1[static_cast<int64_t>(j) * v + b]);
         sq += u * u;
         mx = fmaxf(mx, u);
       }
@@ -629,6 +646,8 @@ struct Ctx {
   Status* status;
   uint64_t timeout_ns;
   bool adjoint = false;  // residual of tbar2 with L^J transposed: sum_ab tbar_ij^ab g_acbd
+  const double* r2 = nullptr;  // excited-state density: the ladder doubles are r0 t2 + r2
+  double r0 = 1.0;
   int err = 0;
   void check(int rc) {
     if (rc && !err) err = rc;
@@ -792,7 +811,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
     c.cuda(cudaMemsetAsync(bnd, 0, 8 * sizeof(unsigned), st));
     k_bound_L<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(sy.L_vv, nj, vv, bnd);
     k_bound_amp<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(
-        c.adjoint ? nullptr : sy.t1, amp, o, v, bnd + 2);
+        c.adjoint ? nullptr : sy.t1, amp, o, v, bnd + 2, c.r2, c.r0);
     c.launched(2);
     if (do_den) {
       k_bound_amp<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(
@@ -808,7 +827,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
   if (minus) c.cuda(cudaMemsetAsync(tm, 0, mat_bytes(P.prec, P.Pom, P.Kvm), st));
   k_pack_tau<T><<<dim3(v, static_cast<unsigned>(P.Pop)), 128, 0, st>>>(
       c.adjoint ? nullptr : sy.t1, c.adjoint ? sy.tbar2 : sy.t2, o, v, tp, P.Kvp, tp_piece, tm, P.Kvm, tm_piece,
-      minus, SC(1));
+      minus, SC(1), c.r2, c.r0);
   c.launched();
 
   double* epart = at<double>(ws, P.o_E);
@@ -976,7 +995,7 @@ static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int whic
 
 static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
                int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream,
-               bool adjoint = false) {
+               bool adjoint = false, const double* const* es_r2 = nullptr, const double* es_r0 = nullptr) {
   if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED && prec != CC_PREC_FP16X2) return CC_ERR_ARG;
   int rc = validate(sys, n_sys, den || want_E || adjoint);
   if (rc) return rc;
@@ -1004,6 +1023,8 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
     double* om = (res && omega) ? omega[i] : nullptr;
     double* Dd = den ? D[i] : nullptr;
     double* Ei = want_E ? E + i : nullptr;
+    c.r2 = es_r2 ? es_r2[i] : nullptr;
+    c.r0 = es_r0 ? es_r0[i] : 1.0;
     if (prec == CC_PREC_MIXED)
       run_system<__nv_bfloat16>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
     else if (prec == CC_PREC_FP16X2)
@@ -1047,6 +1068,15 @@ int cc_ladder_density(const cc_ladder_system* sys, int n_sys, double* const* D, 
                       size_t ws_bytes, void* stream) {
   if (!D) return CC_ERR_ARG;
   return run(sys, n_sys, nullptr, D, nullptr, p, CC_WS_DENSITY, false, true, false, ws, ws_bytes, stream);
+}
+
+int cc_ladder_density_es(const cc_ladder_system* sys, int n_sys, const double* const* R2, const double* R0,
+                         double* const* D, cc_precision p, void* ws, size_t ws_bytes, void* stream) {
+  if (!D || !R2 || !R0 || !sys || n_sys < 1) return CC_ERR_ARG;
+  for (int i = 0; i < n_sys; ++i)
+    if (!R2[i] || !aligned8(R2[i])) return CC_ERR_ARG;
+  return run(sys, n_sys, nullptr, D, nullptr, p, CC_WS_DENSITY, false, true, false, ws, ws_bytes, stream, false, R2,
+             R0);
 }
 
 int cc_ladder_lagrangian(const cc_ladder_system* sys, int n_sys, double* E, double* const* omega_opt, cc_precision p,

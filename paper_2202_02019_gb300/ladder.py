@@ -55,6 +55,8 @@ def load(build_if_missing: bool = True):
     for name in ("cc_ladder_residual", "cc_ladder_density", "cc_ladder_residual_adjoint"):
         getattr(lib, name).argtypes = [SYS, I, PP, I, VP, S, VP]
         getattr(lib, name).restype = I
+    lib.cc_ladder_density_es.argtypes = [SYS, I, PP, ctypes.POINTER(ctypes.c_double), PP, I, VP, S, VP]
+    lib.cc_ladder_density_es.restype = I
     lib.cc_ladder_lagrangian.argtypes = [SYS, I, P, PP, I, VP, S, VP]
     lib.cc_ladder_lagrangian.restype = I
     lib.cc_ladder_step.argtypes = [SYS, I, PP, PP, P, I, VP, S, VP]
@@ -71,6 +73,10 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_launch_count.restype = ctypes.c_longlong
     lib.cc_ladder_lagrangian_noalloc.argtypes = [SYS, I, P, PP, VP]
     lib.cc_ladder_lagrangian_noalloc.restype = I
+    lib.cc_ladder_t1_transform.argtypes = [I, I, I, P, P, P, P, VP]
+    lib.cc_ladder_t1_transform.restype = I
+    lib.cc_ladder_w_backtransform.argtypes = [I, I, I, P, P, P, VP]
+    lib.cc_ladder_w_backtransform.restype = I
     lib.cc_ladder_set_tuning.argtypes = [I, I]
     lib.cc_ladder_set_tuning.restype = I
     lib.cc_ladder_profile.argtypes = [I]
@@ -87,7 +93,8 @@ EXPORTS = (
     "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
     "cc_ladder_profile", "cc_ladder_profile_read", "cc_ladder_lagrangian_noalloc",
-    "cc_ladder_residual_adjoint", "cc_ladder_set_tuning",
+    "cc_ladder_residual_adjoint", "cc_ladder_set_tuning", "cc_ladder_t1_transform",
+    "cc_ladder_w_backtransform", "cc_ladder_density_es",
 )
 
 
@@ -196,6 +203,19 @@ def cc_ladder_density(systems, prec="mixed", ws=None, out=None, stream=None):
     return out
 
 
+def cc_ladder_density_es(systems, R2, R0, prec="mixed", ws=None, out=None, stream=None):
+    """Excited-state density: D with U = R0 * t2 + R2 in place of tau (tbar2 = left doubles L2)."""
+    lib = load()
+    ws = _ws(systems, prec, CC_WS_DENSITY, ws)
+    out = out or [torch.empty_like(s.L_vv) for s in systems]
+    r0 = (ctypes.c_double * len(systems))(*[float(x) for x in R0])
+    for r in R2:
+        _f64(r, "R2")
+    _check(lib.cc_ladder_density_es(_arr(systems), len(systems), _ptrs(R2), r0, _ptrs(out), _prec(prec),
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
 def cc_ladder_lagrangian(systems, omega=None, prec="mixed", ws=None, E=None, stream=None):
     lib = load()
     ws = _ws(systems, prec, CC_WS_LAGRANGIAN, ws)
@@ -264,6 +284,32 @@ def cc_ladder_profile_read():
     ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
     _check(load().cc_ladder_profile_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
     return ms.value, n.value, fl.value
+
+
+def _f64(t, name):
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def cc_ladder_t1_transform(L_vv, L_ov, t1, out=None, stream=None):
+    """vv block of the T1-transformed Cholesky vectors: L_vv - t1^T L_ov per J."""
+    nj, v, _ = L_vv.shape
+    o = t1.shape[0]
+    out = torch.empty_like(L_vv) if out is None else out
+    _check(load().cc_ladder_t1_transform(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(t1, "t1"),
+                                         _f64(out, "out"), _stream(stream)))
+    return out
+
+
+def cc_ladder_w_backtransform(W_vv, t1, out=None, stream=None):
+    """ov block of x^T W y for a vv-only W: -t1 W per J."""
+    nj, v, _ = W_vv.shape
+    o = t1.shape[0]
+    out = torch.empty((nj, o, v), dtype=torch.float64, device=W_vv.device) if out is None else out
+    _check(load().cc_ladder_w_backtransform(o, v, nj, _f64(W_vv, "W_vv"), _f64(t1, "t1"), _f64(out, "out"),
+                                            _stream(stream)))
+    return out
 
 
 def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):

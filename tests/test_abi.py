@@ -80,3 +80,16 @@ def test_noalloc_size_limit_is_host_checked():
     om = (ctypes.c_void_p * n)(*([0x6000] * n))
     assert lib.cc_ladder_lagrangian_noalloc(arr, n, ctypes.c_void_p(0x7000), om, None) == -6
     assert "64 systems" in lad.cc_ladder_strerror(-6)
+
+
+def test_t1_entry_points_host_checks():
+    # argument errors are caught on the host before any device work
+    lib = lad.load()
+    P = ctypes.c_void_p
+    good = [P(0x10000), P(0x20000), P(0x30000)]
+    assert lib.cc_ladder_t1_transform(0, 5, 3, *good, P(0x40000), None) == -1
+    assert lib.cc_ladder_t1_transform(2, 5, 3, None, good[1], good[2], P(0x40000), None) == -1
+    assert lib.cc_ladder_t1_transform(2, 5, 3, *good, P(0x40004), None) == -1          # misaligned
+    assert lib.cc_ladder_t1_transform(2, 5, 3, *good, P(0x10000 + 8), None) == -1      # output overlaps L_vv
+    assert lib.cc_ladder_w_backtransform(2, 5, 0, good[0], good[1], P(0x40000), None) == -1
+    assert lib.cc_ladder_w_backtransform(2, 5, 3, good[0], good[1], P(0x20000), None) == -1  # overlaps t1
