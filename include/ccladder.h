@@ -176,6 +176,36 @@ int cc_ladder_t1_transform(int32_t o, int32_t v, int32_t nj, const double* L_vv,
 int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_vv,
                               const double* t1, double* W_ov, void* stream);
 
+/* MP2-like driver of the doubles equations from the occupied-virtual block
+ * of the Cholesky vectors (Sec. II.A):
+ *     g[i][j][a][b] = g_aibj = sum_J L^J_ia L^J_jb      (t2 layout, [o][o][v][v])
+ * L_ov [nj][o][v] (L^J_ia at (J*o + i)*v + a, symmetric MO vectors: L_ai = L_ia).
+ * An o v x o v contraction over J: FP64 DMMA for CC_PREC_FP64, split BF16
+ * (float-float result) for either split precision.  The output is made
+ * exactly pair symmetric (g_aibj = g_bjai).  Workspace: at least
+ * cc_ladder_mp2_driver_workspace_size() bytes, 256-byte aligned. */
+size_t cc_ladder_mp2_driver_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p);
+int cc_ladder_mp2_driver(int32_t o, int32_t v, int32_t nj, const double* L_ov, double* g,
+                         cc_precision p, void* ws, size_t ws_bytes, void* stream);
+
+/* n_iter Jacobi steps of the doubles amplitude equations restricted to the
+ * ladder and the MP2-like driver (the CC equations of Sec. II.A solved with
+ * the orbital-energy denominators; the paper leaves the solver to its CC
+ * program):
+ *     t' = (g_aibj + (Omega_ij^ab + Omega_ji^ba) / 2) / (eps_i + eps_j - eps_a - eps_b),
+ *     Omega = sum_cd g_acbd tau_ij^cd,  tau = t + t1 (x) t1 with sys->t1 fixed.
+ * sys: L_vv, t1 (may be NULL), t2 = the starting amplitudes (read only),
+ * eps (required).  g_drv: device [o][o][v][v] driver (cc_ladder_mp2_driver).
+ * The final amplitudes go to t2_out (may equal sys->t2); dnorm2 is a device
+ * array of n_iter doubles receiving sum (t' - t)^2 of each step.  One
+ * system per call.  Workspace: cc_ladder_iterate_workspace_size() bytes
+ * (the residual's workspace plus two [o][o][v][v] FP64 buffers).  The
+ * latched status (cc_ladder_status) covers all steps of the call. */
+size_t cc_ladder_iterate_workspace_size(const cc_ladder_system* sys, cc_precision p);
+int cc_ladder_iterate(const cc_ladder_system* sys, const double* g_drv, int n_iter,
+                      double* t2_out, double* dnorm2, cc_precision p,
+                      void* ws, size_t ws_bytes, void* stream);
+
 /* Synchronises `stream`, then returns and clears the device-side status
  * latched in `ws` by earlier calls (CC_OK or CC_ERR_TIMEOUT), or
  * CC_ERR_CUDA if the stream reports an error. */

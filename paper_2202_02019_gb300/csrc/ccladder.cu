@@ -411,6 +411,46 @@ __global__ void k_update(const double* __restrict__ t2, const double* __restrict
   }
 }
 
+// MP2-like driver from the contraction output G[(j,b)][(i,a)] (ld = o v):
+// g[i][j][a][b] = (G[(i,a),(j,b)] + G[(j,b),(i,a)]) / 2, exactly pair symmetric
+template <typename S>
+__global__ void k_driver_to_t2(const S* __restrict__ G, int o, int v, double* __restrict__ g) {
+  const int64_t ov = static_cast<int64_t>(o) * v, total = ov * ov;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(k % v);
+    const int a = static_cast<int>((k / v) % v);
+    const int j = static_cast<int>((k / (static_cast<int64_t>(v) * v)) % o);
+    const int i = static_cast<int>(k / (static_cast<int64_t>(v) * v * o));
+    const int64_t ia = static_cast<int64_t>(i) * v + a, jb = static_cast<int64_t>(j) * v + b;
+    g[k] = 0.5 * (Ar<S>::to_d(G[jb * ov + ia]) + Ar<S>::to_d(G[ia * ov + jb]));
+  }
+}
+
+// Jacobi step t' = (g + (Omega_ij^ab + Omega_ji^ba) / 2) / (e_i + e_j - e_a - e_b)
+// and per-block partial sums of (t' - t)^2
+__global__ void k_jacobi(const double* __restrict__ g, const double* __restrict__ om, const double* __restrict__ t,
+                         const double* __restrict__ eps, int o, int v, double* __restrict__ tn,
+                         double* __restrict__ part) {
+  const int64_t vv = static_cast<int64_t>(v) * v, total = static_cast<int64_t>(o) * o * vv;
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(k % v);
+    const int a = static_cast<int>((k / v) % v);
+    const int j = static_cast<int>((k / vv) % o);
+    const int i = static_cast<int>(k / (vv * o));
+    const int64_t kt = (static_cast<int64_t>(j) * o + i) * vv + static_cast<int64_t>(b) * v + a;
+    const double den = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+    const double x = (g[k] + 0.5 * (om[k] + om[kt])) / den;
+    const double d = x - t[k];
+    s += d * d;
+    tn[k] = x;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void k_debug_wait(const int* flag, unsigned long long timeout_ns, Status* st) {
   const volatile int* f = flag;
   const uint64_t t0 = globaltimer();
@@ -995,7 +1035,8 @@ static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int whic
 
 static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
                int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream,
-               bool adjoint = false, const double* const* es_r2 = nullptr, const double* es_r0 = nullptr) {
+               bool adjoint = false, const double* const* es_r2 = nullptr, const double* es_r0 = nullptr,
+               bool clear_status = true) {
   if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED && prec != CC_PREC_FP16X2) return CC_ERR_ARG;
   int rc = validate(sys, n_sys, den || want_E || adjoint);
   if (rc) return rc;
@@ -1016,7 +1057,7 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
   c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
   c.adjoint = adjoint;
   // every call starts from a clear status word; cc_ladder_status() reads it
-  c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), c.st));
+  if (clear_status) c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), c.st));
   for (int i = 0; i < n_sys && !c.err; ++i) {
     Plan P;
     make_plan(sys[i], prec, which, P);
@@ -1035,11 +1076,125 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
   return c.err;
 }
 
+// ---------------------------------------------------------------------------
+// doubles amplitude iteration (MP2-like driver + ladder + Jacobi step)
+// ---------------------------------------------------------------------------
+// driver workspace: status header, L_ov K-major in the operand format, G output
+struct DriverPlan {
+  int64_t ov, Kj;
+  size_t o_LT, o_G, total;
+};
+static DriverPlan driver_plan(int o, int v, int nj, int prec) {
+  DriverPlan d;
+  d.ov = static_cast<int64_t>(o) * v;
+  d.Kj = rup(nj, 64);
+  const int op = prec == CC_PREC_FP64 ? CC_PREC_FP64 : CC_PREC_MIXED;  // split BF16 for every split path
+  d.o_LT = kStatusBytes;
+  d.o_G = d.o_LT + rup(static_cast<int64_t>(mat_bytes(op, d.ov, d.Kj)), 256);
+  d.total = d.o_G + rup(d.ov * d.ov * 8, 256);
+  return d;
+}
+
+template <typename T>
+static int run_driver(int o, int v, int nj, const double* L_ov, double* g, const DriverPlan& d, char* ws,
+                      cudaStream_t st) {
+  using S = typename Path<T>::S;
+  Ctx c;
+  c.st = st;
+  c.status = reinterpret_cast<Status*>(ws);
+  c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
+  c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
+  T* LT = at<T>(ws, d.o_LT);
+  const int64_t piece = d.ov * d.Kj;
+  k_prep_LT<T><<<dim3(static_cast<unsigned>((d.ov + 31) / 32), static_cast<unsigned>(d.Kj / 32)), dim3(32, 8), 0,
+                 st>>>(L_ov, nj, d.ov, v, 0, LT, d.Kj, piece, nullptr);
+  c.launched();
+  S* G = at<S>(ws, d.o_G);
+  const Gm gm = {LT, d.Kj, d.ov, d.Kj, piece, LT, d.Kj, d.ov, d.Kj, piece, d.ov, d.ov, d.Kj, G, d.ov, false};
+  run_gemms<T>(&gm, 1, c);
+  k_driver_to_t2<S><<<4096, 256, 0, st>>>(G, o, v, g);
+  c.launched();
+  return c.err;
+}
+
+static size_t iterate_need(const cc_ladder_system* sys, int prec, size_t* res_bytes) {
+  const size_t r = ws_need(sys, 1, prec, CC_WS_RESIDUAL);
+  if (!r) return 0;
+  const size_t n = static_cast<size_t>(sys->o) * sys->o * sys->v * sys->v * 8;
+  *res_bytes = static_cast<size_t>(rup(static_cast<int64_t>(r), 256));
+  return *res_bytes + 2 * static_cast<size_t>(rup(static_cast<int64_t>(n), 256)) + 1024 * 8;
+}
+
 }  // namespace ccl
 
 using namespace ccl;
 
 extern "C" {
+
+size_t cc_ladder_mp2_driver_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p) {
+  if (o < 1 || v < 1 || nj < 1 || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2)) return 0;
+  return driver_plan(o, v, nj, p).total;
+}
+
+int cc_ladder_mp2_driver(int32_t o, int32_t v, int32_t nj, const double* L_ov, double* g, cc_precision p, void* ws,
+                         size_t ws_bytes, void* stream) {
+  if (o < 1 || v < 1 || nj < 1 || !L_ov || !g || !aligned8(L_ov) || !aligned8(g)) return CC_ERR_ARG;
+  if (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) return CC_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  if (const int rc = check_device()) return rc;
+  const DriverPlan d = driver_plan(o, v, nj, p);
+  if (ws_bytes < d.total) return CC_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p == CC_PREC_FP64) return run_driver<double>(o, v, nj, L_ov, g, d, static_cast<char*>(ws), st);
+  return run_driver<__nv_bfloat16>(o, v, nj, L_ov, g, d, static_cast<char*>(ws), st);
+}
+
+size_t cc_ladder_iterate_workspace_size(const cc_ladder_system* sys, cc_precision p) {
+  if (validate(sys, 1, false) || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2)) return 0;
+  size_t r = 0;
+  return iterate_need(sys, p, &r);
+}
+
+int cc_ladder_iterate(const cc_ladder_system* sys, const double* g_drv, int n_iter, double* t2_out, double* dnorm2,
+                      cc_precision p, void* ws, size_t ws_bytes, void* stream) {
+  if (validate(sys, 1, false) || !sys->eps || !g_drv || !t2_out || !dnorm2 || n_iter < 1) return CC_ERR_ARG;
+  if (!aligned8(g_drv) || !aligned8(t2_out) || !aligned8(dnorm2)) return CC_ERR_ARG;
+  if (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) return CC_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  if (const int rc = check_device()) return rc;
+  size_t rb = 0;
+  const size_t need = iterate_need(sys, p, &rb);
+  if (!need) return CC_ERR_ARG;
+  if (ws_bytes < need) return CC_ERR_WORKSPACE;
+  char* w = static_cast<char*>(ws);
+  const size_t n = static_cast<size_t>(sys->o) * sys->o * sys->v * sys->v;
+  const size_t nb = static_cast<size_t>(rup(static_cast<int64_t>(n * 8), 256));
+  double* om = reinterpret_cast<double*>(w + rb);
+  double* tmp = reinterpret_cast<double*>(w + rb + nb);
+  double* part = reinterpret_cast<double*>(w + rb + 2 * nb);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double* cur = sys->t2;
+  for (int k = 0; k < n_iter; ++k) {
+    double* target = ((n_iter - 1 - k) % 2 == 0) ? t2_out : tmp;
+    cc_ladder_system sk = *sys;
+    sk.t2 = cur;
+    double* omp[1] = {om};
+    const int rc = run(&sk, 1, omp, nullptr, nullptr, p, CC_WS_RESIDUAL, true, false, false, ws, rb, stream, false,
+                       nullptr, nullptr, k == 0);
+    if (rc) return rc;
+    k_jacobi<<<1024, 256, 0, st>>>(g_drv, om, cur, sys->eps, sys->o, sys->v, target, part);
+    k_sum_final<<<1, 1024, 0, st>>>(part, 1024, dnorm2 + k);
+    count_launch(2);
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+      note_cuda(e);
+      return CC_ERR_CUDA;
+    }
+    cur = target;
+  }
+  return CC_OK;
+}
+
 
 size_t cc_ladder_workspace_size(const cc_ladder_system* sys, int n_sys, cc_precision p, int which) {
   if (validate(sys, n_sys, false) || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) ||

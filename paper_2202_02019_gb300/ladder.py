@@ -77,6 +77,14 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_t1_transform.restype = I
     lib.cc_ladder_w_backtransform.argtypes = [I, I, I, P, P, P, VP]
     lib.cc_ladder_w_backtransform.restype = I
+    lib.cc_ladder_mp2_driver_workspace_size.argtypes = [I, I, I, I]
+    lib.cc_ladder_mp2_driver_workspace_size.restype = S
+    lib.cc_ladder_mp2_driver.argtypes = [I, I, I, P, P, I, VP, S, VP]
+    lib.cc_ladder_mp2_driver.restype = I
+    lib.cc_ladder_iterate_workspace_size.argtypes = [SYS, I]
+    lib.cc_ladder_iterate_workspace_size.restype = S
+    lib.cc_ladder_iterate.argtypes = [SYS, P, I, P, P, I, VP, S, VP]
+    lib.cc_ladder_iterate.restype = I
     lib.cc_ladder_set_tuning.argtypes = [I, I]
     lib.cc_ladder_set_tuning.restype = I
     lib.cc_ladder_profile.argtypes = [I]
@@ -94,7 +102,8 @@ EXPORTS = (
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
     "cc_ladder_profile", "cc_ladder_profile_read", "cc_ladder_lagrangian_noalloc",
     "cc_ladder_residual_adjoint", "cc_ladder_set_tuning", "cc_ladder_t1_transform",
-    "cc_ladder_w_backtransform", "cc_ladder_density_es",
+    "cc_ladder_w_backtransform", "cc_ladder_density_es", "cc_ladder_mp2_driver_workspace_size",
+    "cc_ladder_mp2_driver", "cc_ladder_iterate_workspace_size", "cc_ladder_iterate",
 )
 
 
@@ -310,6 +319,36 @@ def cc_ladder_w_backtransform(W_vv, t1, out=None, stream=None):
     _check(load().cc_ladder_w_backtransform(o, v, nj, _f64(W_vv, "W_vv"), _f64(t1, "t1"), _f64(out, "out"),
                                             _stream(stream)))
     return out
+
+
+def cc_ladder_mp2_driver(L_ov, prec="mixed", ws=None, out=None, stream=None):
+    """g[i, j, a, b] = sum_J L_ov[J, i, a] L_ov[J, j, b] (the MP2-like driver)."""
+    lib = load()
+    nj, o, v = L_ov.shape
+    n = int(lib.cc_ladder_mp2_driver_workspace_size(o, v, nj, _prec(prec)))
+    if n == 0:
+        raise LadderError(-1, "invalid sizes for the driver workspace")
+    ws = torch.empty(n, dtype=torch.uint8, device=L_ov.device) if ws is None else ws
+    out = torch.empty((o, o, v, v), dtype=torch.float64, device=L_ov.device) if out is None else out
+    _check(lib.cc_ladder_mp2_driver(o, v, nj, _f64(L_ov, "L_ov"), _f64(out, "out"), _prec(prec),
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out
+
+
+def cc_ladder_iterate(system, g_drv, n_iter, prec="mixed", ws=None, out=None, dnorm2=None, stream=None):
+    """n_iter Jacobi steps of the ladder + driver doubles equations; returns (t2, sum (t' - t)^2 per step)."""
+    lib = load()
+    arr = _arr([system])
+    if ws is None:
+        n = int(lib.cc_ladder_iterate_workspace_size(arr, _prec(prec)))
+        if n == 0:
+            raise LadderError(-1, "invalid system for the iteration workspace")
+        ws = torch.empty(n, dtype=torch.uint8, device=system.L_vv.device)
+    out = torch.empty_like(system.t2) if out is None else out
+    dnorm2 = torch.empty(n_iter, dtype=torch.float64, device=system.L_vv.device) if dnorm2 is None else dnorm2
+    _check(lib.cc_ladder_iterate(arr, _f64(g_drv, "g_drv"), int(n_iter), _f64(out, "out"), _f64(dnorm2, "dnorm2"),
+                                 _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return out, dnorm2
 
 
 def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):
