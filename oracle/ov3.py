@@ -1,0 +1,47 @@
+"""FP64 oracle for the OV^3 ground-state density contributions to the
+three-index intermediates (test infrastructure only, like the rest of
+``oracle``).
+
+Ground state, App. A:  d_abci = 0  and  d_abic = L^a_m t~^cb_im R0  with
+t~_ij^ab = 2 t_ij^ab - t_ji^ab (Table I) and L^a_m the singles multipliers.
+Sec. II.C builds the OV^3 blocks' contributions to W^K_pq = sum_rs d_pqrs
+Z^K_rs directly, never storing the density:
+
+    W_ab^K = sum_ic d_abic Z^K_ic = R0 L^a_m Y~^K_bm,   Y~^K_bm = t~^cb_im Z^K_ic   (Table I)
+    W_ic^K = sum_ab d_abic Z^K_ab = R0 t~^cb_im O^K_bm,  O^K_bm = L^a_m Z^K_ab
+
+with L^K in place of Z^K, as for the V^4 part (D).  ``*_explicit`` forms the
+OV^3 density; ``w_ov3_gs`` is the factorised form.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["t_tilde", "density_abic_gs", "w_from_abic", "w_ov3_gs"]
+
+
+def t_tilde(t2):
+    """t~_ij^ab = 2 t_ij^ab - t_ji^ab."""
+    t2 = np.asarray(t2, dtype=np.float64)
+    return 2.0 * t2 - t2.transpose(1, 0, 2, 3)
+
+
+def density_abic_gs(tbar1, t2, R0):
+    """d[a, b, i, c] = R0 sum_m L^a_m t~^cb_im (tbar1[m, a] = L^a_m)."""
+    tt = t_tilde(t2)                                    # tt[i, m, c, b] = t~^cb_im
+    return R0 * np.einsum("ma,imcb->abic", np.asarray(tbar1, dtype=np.float64), tt)
+
+
+def w_from_abic(d, L_vv, L_ov):
+    """(W_vv[K, a, b], W_ov[K, i, c]) = (sum_ic d_abic L^K_ic, sum_ab d_abic L^K_ab)."""
+    return np.einsum("abic,Kic->Kab", d, L_ov), np.einsum("abic,Kab->Kic", d, L_vv)
+
+
+def w_ov3_gs(tbar1, t2, R0, L_vv, L_ov):
+    """The factorised form through Y~ and O (no OV^3 array)."""
+    tt = t_tilde(t2)
+    Y = np.einsum("imcb,Kic->Kbm", tt, L_ov)           # Y~^K_bm
+    W_vv = R0 * np.einsum("ma,Kbm->Kab", tbar1, Y)
+    Om = np.einsum("ma,Kab->Kbm", tbar1, L_vv)         # O^K_bm
+    W_ov = R0 * np.einsum("imcb,Kbm->Kic", tt, Om)
+    return W_vv, W_ov
