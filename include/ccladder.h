@@ -176,6 +176,23 @@ int cc_ladder_t1_transform(int32_t o, int32_t v, int32_t nj, const double* L_vv,
 int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_vv,
                               const double* t1, double* W_ov, void* stream);
 
+/* Ground-state OV^3 density contributions to the three-index intermediates
+ * (Sec. II.C with App. A: d_abci = 0 and d_abic = L^a_m t~^cb_im R0 in the
+ * ground state, t~_ij^ab = 2 t_ij^ab - t_ji^ab), built without the OV^3 array
+ * through the intermediates of Table I, with L^K in place of Z^K (as for D):
+ *     W_vv[K][a][b] = R0 sum_m tbar1[m][a] Y~^K_bm,   Y~^K_bm = sum_ic t~^cb_im L^K_ic
+ *     W_ov[K][i][c] = R0 sum_mb t~^cb_im O^K_bm,      O^K_bm  = sum_a tbar1[m][a] L^K_ab
+ * tbar1 [o][v] holds the singles multipliers L^a_m at m*v + a; t2 [o][o][v][v]
+ * (pair symmetric); L_vv [nj][v][v]; L_ov [nj][o][v].  Outputs are
+ * overwritten: W_vv [nj][v][v], W_ov [nj][o][v].  The two (o v) x N_J
+ * contractions run on FP64 DMMA for CC_PREC_FP64 and on split BF16 for either
+ * split precision; the small ones in FP64.  Workspace:
+ * cc_ladder_ov3_workspace_size() bytes, 256-byte aligned. */
+size_t cc_ladder_ov3_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p);
+int cc_ladder_ov3_gs(int32_t o, int32_t v, int32_t nj, const double* L_vv, const double* L_ov,
+                     const double* t2, const double* tbar1, double R0, double* W_vv,
+                     double* W_ov, cc_precision p, void* ws, size_t ws_bytes, void* stream);
+
 /* MP2-like driver of the doubles equations from the occupied-virtual block
  * of the Cholesky vectors (Sec. II.A):
  *     g[i][j][a][b] = g_aibj = sum_J L^J_ia L^J_jb      (t2 layout, [o][o][v][v])

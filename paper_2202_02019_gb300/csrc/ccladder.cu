@@ -451,6 +451,44 @@ __global__ void k_jacobi(const double* __restrict__ g, const double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// t~ matrix for the OV^3 contributions: P[(i,c)][(m,b)] = 2 t_im^cb - t_mi^cb
+// (zero for columns past o v), split into the operand format
+template <typename T>
+__global__ void k_pack_ttilde(const double* __restrict__ t2, int o, int v, T* __restrict__ P, int64_t ld,
+                              int64_t piece) {
+  const int64_t ov = static_cast<int64_t>(o) * v, vv = static_cast<int64_t>(v) * v;
+  const int64_t r = blockIdx.x;  // (i, c)
+  const int i = static_cast<int>(r / v), c = static_cast<int>(r % v);
+  for (int64_t k = threadIdx.x; k < ld; k += blockDim.x) {
+    double x = 0.0;
+    if (k < ov) {
+      const int m = static_cast<int>(k / v), b = static_cast<int>(k % v);
+      x = 2.0 * t2[(static_cast<int64_t>(i) * o + m) * vv + static_cast<int64_t>(c) * v + b] -
+          t2[(static_cast<int64_t>(m) * o + i) * vv + static_cast<int64_t>(c) * v + b];
+    }
+    Store<T>::put(P, r * ld + k, piece, x, 1.f);
+  }
+}
+
+// out[r][k] = src[r][k] (k < cols), 0 up to ld, in the operand format
+template <typename T>
+__global__ void k_pack_rows(const double* __restrict__ src, int64_t rows, int64_t cols, T* __restrict__ out,
+                            int64_t ld, int64_t piece) {
+  const int64_t total = rows * ld;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = q / ld, k = q % ld;
+    Store<T>::put(out, q, piece, k < cols ? src[r * cols + k] : 0.0, 1.f);
+  }
+}
+
+template <typename S>
+__global__ void k_to_f64_scaled(const S* __restrict__ in, double* __restrict__ out, int64_t n, double scale) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[k] = scale * Ar<S>::to_d(in[k]);
+}
+
 __global__ void k_debug_wait(const int* flag, unsigned long long timeout_ns, Status* st) {
   const volatile int* f = flag;
   const uint64_t t0 = globaltimer();
@@ -1125,11 +1163,96 @@ static size_t iterate_need(const cc_ladder_system* sys, int prec, size_t* res_by
   return *res_bytes + 2 * static_cast<size_t>(rup(static_cast<int64_t>(n), 256)) + 1024 * 8;
 }
 
+// ---------------------------------------------------------------------------
+// ground-state OV^3 contributions to the three-index intermediates
+// ---------------------------------------------------------------------------
+struct Ov3Plan {
+  int64_t ov, Kov;
+  size_t o_P, o_B, o_G, o_Y, total;
+};
+static Ov3Plan ov3_plan(int o, int v, int nj, int prec) {
+  Ov3Plan d;
+  d.ov = static_cast<int64_t>(o) * v;
+  d.Kov = rup(d.ov, 64);
+  const int op = prec == CC_PREC_FP64 ? CC_PREC_FP64 : CC_PREC_MIXED;
+  d.o_P = kStatusBytes;
+  d.o_B = d.o_P + rup(static_cast<int64_t>(mat_bytes(op, d.ov, d.Kov)), 256);
+  d.o_G = d.o_B + rup(static_cast<int64_t>(mat_bytes(op, nj, d.Kov)), 256);
+  d.o_Y = d.o_G + rup(static_cast<int64_t>(nj) * d.ov * 8, 256);
+  d.total = d.o_Y + rup(static_cast<int64_t>(nj) * d.ov * 8, 256);
+  return d;
+}
+
+// W_ab^K = R0 sum_m L^a_m Y~^K_bm,  Y~^K_bm = sum_ic t~^cb_im L^K_ic
+// W_ic^K = R0 sum_mb t~^cb_im O^K_bm, O^K_bm = sum_a L^a_m L^K_ab
+// The t~ matrix P[(i,c)][(m,b)] is symmetric for pair-symmetric t2, so it is
+// the A operand of both (o v) x N_J contractions.
+template <typename T>
+static int run_ov3(int o, int v, int nj, const double* L_vv, const double* L_ov, const double* t2,
+                   const double* tbar1, double R0, double* W_vv, double* W_ov, const Ov3Plan& d, char* ws,
+                   cudaStream_t st) {
+  using S = typename Path<T>::S;
+  Ctx c;
+  c.st = st;
+  c.status = reinterpret_cast<Status*>(ws);
+  c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
+  c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
+  T* P = at<T>(ws, d.o_P);
+  T* B = at<T>(ws, d.o_B);
+  S* G = at<S>(ws, d.o_G);
+  double* Y = at<double>(ws, d.o_Y);
+  const int64_t p_piece = d.ov * d.Kov, b_piece = static_cast<int64_t>(nj) * d.Kov;
+  const int64_t nov = static_cast<int64_t>(nj) * d.ov;
+  const unsigned grid_e = static_cast<unsigned>(std::min<int64_t>(4096, (nov + 255) / 256));
+  k_pack_ttilde<T><<<static_cast<unsigned>(d.ov), 256, 0, st>>>(t2, o, v, P, d.Kov, p_piece);
+  k_pack_rows<T><<<4096, 256, 0, st>>>(L_ov, nj, d.ov, B, d.Kov, b_piece);
+  c.launched(2);
+  const Gm g1 = {P, d.Kov, d.ov, d.Kov, p_piece, B, d.Kov, nj, d.Kov, b_piece, d.ov, nj, d.Kov, G, d.ov, false};
+  run_gemms<T>(&g1, 1, c);  // G[K][(m,b)] = Y~^K_bm
+  k_to_f64_scaled<S><<<grid_e, 256, 0, st>>>(G, Y, nov, 1.0);
+  c.launched();
+  // W_vv[K][a][b] = R0 sum_m tbar1[m][a] Y[K][m][b]
+  c.check(batched_gemm_f64(v, v, o, nj, tbar1, 1, v, Y, d.ov, v, nullptr, 0, 0, R0, W_vv,
+                           static_cast<int64_t>(v) * v, v, st));
+  // O[K][m][b] = sum_a tbar1[m][a] L_vv[K][a][b]   (into Y, whose contents are used up)
+  c.check(batched_gemm_f64(o, v, v, nj, tbar1, v, 1, L_vv, static_cast<int64_t>(v) * v, v, nullptr, 0, 0, 1.0, Y,
+                           d.ov, v, st));
+  k_pack_rows<T><<<4096, 256, 0, st>>>(Y, nj, d.ov, B, d.Kov, b_piece);
+  c.launched();
+  const Gm g2 = {P, d.Kov, d.ov, d.Kov, p_piece, B, d.Kov, nj, d.Kov, b_piece, d.ov, nj, d.Kov, G, d.ov, false};
+  run_gemms<T>(&g2, 1, c);  // G[K][(i,c)] = W_ic^K / R0
+  k_to_f64_scaled<S><<<grid_e, 256, 0, st>>>(G, W_ov, nov, R0);
+  c.launched();
+  return c.err;
+}
+
 }  // namespace ccl
 
 using namespace ccl;
 
 extern "C" {
+
+size_t cc_ladder_ov3_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p) {
+  if (o < 1 || v < 1 || nj < 1 || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2)) return 0;
+  return ov3_plan(o, v, nj, p).total;
+}
+
+int cc_ladder_ov3_gs(int32_t o, int32_t v, int32_t nj, const double* L_vv, const double* L_ov, const double* t2,
+                     const double* tbar1, double R0, double* W_vv, double* W_ov, cc_precision p, void* ws,
+                     size_t ws_bytes, void* stream) {
+  if (o < 1 || v < 1 || nj < 1 || !L_vv || !L_ov || !t2 || !tbar1 || !W_vv || !W_ov) return CC_ERR_ARG;
+  if (!aligned8(L_vv) || !aligned8(L_ov) || !aligned8(t2) || !aligned8(tbar1) || !aligned8(W_vv) || !aligned8(W_ov))
+    return CC_ERR_ARG;
+  if (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) return CC_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  if (const int rc = check_device()) return rc;
+  const Ov3Plan d = ov3_plan(o, v, nj, p);
+  if (ws_bytes < d.total) return CC_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p == CC_PREC_FP64)
+    return run_ov3<double>(o, v, nj, L_vv, L_ov, t2, tbar1, R0, W_vv, W_ov, d, static_cast<char*>(ws), st);
+  return run_ov3<__nv_bfloat16>(o, v, nj, L_vv, L_ov, t2, tbar1, R0, W_vv, W_ov, d, static_cast<char*>(ws), st);
+}
 
 size_t cc_ladder_mp2_driver_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p) {
   if (o < 1 || v < 1 || nj < 1 || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2)) return 0;

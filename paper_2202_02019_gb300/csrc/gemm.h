@@ -47,6 +47,14 @@ struct GemmOp {
 int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream);
 int gemm_f64(const GemmOp& op, cudaStream_t stream);
 
+// C_J = X_J + alpha * A B_J for J < nb, FP64 (csrc/t1.cu): A element (m, k) at
+// m * a_sm + k * a_sk, shared by every J; B_J [K][N], X_J and C_J [M][N]
+// row-major with leading dimensions ldb, ldx, ldc and J strides b_sj, x_sj,
+// c_sj; X may be null.  Returns 0 or CC_ERR_CUDA.
+int batched_gemm_f64(int M, int N, int K, int nb, const double* A, int64_t a_sm, int64_t a_sk, const double* B,
+                     int64_t b_sj, int64_t ldb, const double* X, int64_t x_sj, int64_t ldx, double alpha, double* C,
+                     int64_t c_sj, int64_t ldc, cudaStream_t st);
+
 // Records the text of a failed CUDA call for cc_ladder_strerror.
 void note_cuda(cudaError_t e);
 

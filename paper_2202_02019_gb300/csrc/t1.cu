@@ -98,9 +98,11 @@ bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0;
 // true if [p, p + n) and [q, q + m) (doubles) overlap
 bool overlap(const double* p, int64_t n, const double* q, int64_t m) { return p < q + m && q < p + n; }
 
-int launch(int M, int N, int K, int nb, const double* A, int64_t a_sm, int64_t a_sk, const double* B, int64_t b_sj,
-           int64_t ldb, const double* X, int64_t x_sj, int64_t ldx, double alpha, double* C, int64_t c_sj,
-           int64_t ldc, cudaStream_t st) {
+}  // namespace
+
+int batched_gemm_f64(int M, int N, int K, int nb, const double* A, int64_t a_sm, int64_t a_sk, const double* B,
+                     int64_t b_sj, int64_t ldb, const double* X, int64_t x_sj, int64_t ldx, double alpha, double* C,
+                     int64_t c_sj, int64_t ldc, cudaStream_t st) {
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, nb < 65535 ? nb : 65535);
   k_batched_gemm_f64<<<grid, NT, 0, st>>>(M, N, K, nb, A, a_sm, a_sk, B, b_sj, ldb, X, x_sj, ldx, alpha, C, c_sj,
                                           ldc);
@@ -113,7 +115,6 @@ int launch(int M, int N, int K, int nb, const double* A, int64_t a_sm, int64_t a
   return CC_OK;
 }
 
-}  // namespace
 }  // namespace ccl
 
 using namespace ccl;
@@ -130,8 +131,9 @@ int cc_ladder_t1_transform(int32_t o, int32_t v, int32_t nj, const double* L_vv,
     return CC_ERR_ARG;
   if (const int rc = device_ok()) return rc;
   // M = a (v), N = c (v), K = i (o): A[a][i] = t1[i][a], B_J[i][c] = L_ov[J][i][c]
-  return launch(v, v, o, nj, t1, 1, v, L_ov, static_cast<int64_t>(o) * v, v, L_vv, static_cast<int64_t>(v) * v, v,
-                -1.0, L_vv_t1, static_cast<int64_t>(v) * v, v, static_cast<cudaStream_t>(stream));
+  return batched_gemm_f64(v, v, o, nj, t1, 1, v, L_ov, static_cast<int64_t>(o) * v, v, L_vv,
+                          static_cast<int64_t>(v) * v, v, -1.0, L_vv_t1, static_cast<int64_t>(v) * v, v,
+                          static_cast<cudaStream_t>(stream));
 }
 
 int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_vv, const double* t1, double* W_ov,
@@ -142,8 +144,8 @@ int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_
   if (overlap(W_ov, nov, W_vv, nvv) || overlap(W_ov, nov, t1, static_cast<int64_t>(o) * v)) return CC_ERR_ARG;
   if (const int rc = device_ok()) return rc;
   // M = i (o), N = c (v), K = a (v): A[i][a] = t1[i][a], B_J[a][c] = W_vv[J][a][c]
-  return launch(o, v, v, nj, t1, v, 1, W_vv, static_cast<int64_t>(v) * v, v, nullptr, 0, 0, -1.0, W_ov,
-                static_cast<int64_t>(o) * v, v, static_cast<cudaStream_t>(stream));
+  return batched_gemm_f64(o, v, v, nj, t1, v, 1, W_vv, static_cast<int64_t>(v) * v, v, nullptr, 0, 0, -1.0, W_ov,
+                          static_cast<int64_t>(o) * v, v, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -85,6 +85,10 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_iterate_workspace_size.restype = S
     lib.cc_ladder_iterate.argtypes = [SYS, P, I, P, P, I, VP, S, VP]
     lib.cc_ladder_iterate.restype = I
+    lib.cc_ladder_ov3_workspace_size.argtypes = [I, I, I, I]
+    lib.cc_ladder_ov3_workspace_size.restype = S
+    lib.cc_ladder_ov3_gs.argtypes = [I, I, I, P, P, P, P, ctypes.c_double, P, P, I, VP, S, VP]
+    lib.cc_ladder_ov3_gs.restype = I
     lib.cc_ladder_set_tuning.argtypes = [I, I]
     lib.cc_ladder_set_tuning.restype = I
     lib.cc_ladder_profile.argtypes = [I]
@@ -104,6 +108,7 @@ EXPORTS = (
     "cc_ladder_residual_adjoint", "cc_ladder_set_tuning", "cc_ladder_t1_transform",
     "cc_ladder_w_backtransform", "cc_ladder_density_es", "cc_ladder_mp2_driver_workspace_size",
     "cc_ladder_mp2_driver", "cc_ladder_iterate_workspace_size", "cc_ladder_iterate",
+    "cc_ladder_ov3_workspace_size", "cc_ladder_ov3_gs",
 )
 
 
@@ -349,6 +354,23 @@ def cc_ladder_iterate(system, g_drv, n_iter, prec="mixed", ws=None, out=None, dn
     _check(lib.cc_ladder_iterate(arr, _f64(g_drv, "g_drv"), int(n_iter), _f64(out, "out"), _f64(dnorm2, "dnorm2"),
                                  _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return out, dnorm2
+
+
+def cc_ladder_ov3_gs(L_vv, L_ov, t2, tbar1, R0=1.0, prec="mixed", ws=None, stream=None):
+    """Ground-state OV^3 contributions (W_vv [nj, v, v], W_ov [nj, o, v])."""
+    lib = load()
+    nj, o, v = L_ov.shape
+    if ws is None:
+        n = int(lib.cc_ladder_ov3_workspace_size(o, v, nj, _prec(prec)))
+        if n == 0:
+            raise LadderError(-1, "invalid sizes for the OV^3 workspace")
+        ws = torch.empty(n, dtype=torch.uint8, device=L_vv.device)
+    W_vv = torch.empty_like(L_vv)
+    W_ov = torch.empty_like(L_ov)
+    _check(lib.cc_ladder_ov3_gs(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(t2, "t2"),
+                                _f64(tbar1, "tbar1"), float(R0), _f64(W_vv, "W_vv"), _f64(W_ov, "W_ov"),
+                                _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return W_vv, W_ov
 
 
 def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):
