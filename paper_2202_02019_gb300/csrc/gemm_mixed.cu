@@ -67,7 +67,7 @@ constexpr int A_HALF = A_PIECE / CLUSTER; // bytes of one piece's row slice
 constexpr int B_PIECE = BN * BK * 2;      // 16384 B
 constexpr int SMEM_BYTES = 196608 + 1024 + 256;  // stages * stage bytes is 192 KB for both schemes
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int FOLD = 8;                   // H windows summed in FP32 before the error-free fold
+constexpr int FOLD = 32;                  // H windows summed in FP32 before the error-free fold
 constexpr uint32_t COL_H0 = 0, COL_H1 = 128, COL_L = 256, COL_LO = 384;
 constexpr int NDRAIN = 16;                // draining warps (4 per TMEM lane quarter)
 constexpr int NTHREADS = (2 + NDRAIN) * 32;
@@ -134,7 +134,9 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += e;
 }
 
-// acc += DCOLS TMEM columns of this thread's row (plain round-to-nearest adds)
+// acc += DCOLS TMEM columns of this thread's row (round-to-nearest adds, two
+// lanes per packed FP32x2 instruction: the drain's instructions share issue
+// slots with the MMA and TMA warps, so fewer of them is measurably faster)
 __device__ __forceinline__ void add_cols(uint32_t src, float (&acc)[DCOLS]) {
 #pragma unroll
   for (int c = 0; c < DCOLS; c += 16) {
@@ -142,7 +144,13 @@ __device__ __forceinline__ void add_cols(uint32_t src, float (&acc)[DCOLS]) {
     tmem_ld16(src + c, r);
     tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[c + j] += __uint_as_float(r[j]);
+    for (int j = 0; j < 16; j += 2) {
+      unsigned long long a2, r2, s2;
+      asm("mov.b64 %0, {%1, %2};" : "=l"(a2) : "f"(acc[c + j]), "f"(acc[c + j + 1]));
+      asm("mov.b64 %0, {%1, %2};" : "=l"(r2) : "r"(r[j]), "r"(r[j + 1]));
+      asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s2) : "l"(a2), "l"(r2));
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[c + j]), "=f"(acc[c + j + 1]) : "l"(s2));
+    }
   }
 }
 
