@@ -823,6 +823,7 @@ struct Gm {
   bool acc;
   const float* sa = nullptr;  // operand scales (FP16 two-piece path)
   const float* sb = nullptr;
+  int64_t tri = 0;            // upper block triangle only (see GemmOp::tri)
 };
 
 // K chunk for the FP64 path: whole K unless the launch would have fewer
@@ -843,7 +844,7 @@ static void run_gemms(const Gm* g, int n, Ctx& c) {
     GemmOp& o = ops[i];
     o.A = g[i].A; o.lda = g[i].lda; o.a_rows = g[i].a_rows; o.a_cols = g[i].a_cols; o.a_piece = g[i].a_piece;
     o.B = g[i].B; o.ldb = g[i].ldb; o.b_rows = g[i].b_rows; o.b_cols = g[i].b_cols; o.b_piece = g[i].b_piece;
-    o.M = g[i].M; o.N = g[i].N; o.K = g[i].K; o.out = g[i].out; o.ldo = g[i].ldo;
+    o.M = g[i].M; o.N = g[i].N; o.K = g[i].K; o.out = g[i].out; o.ldo = g[i].ldo; o.tri = g[i].tri;
     o.status = c.status; o.timeout_ns = c.timeout_ns;
   }
   if (Path<T>::mixed) {
@@ -982,7 +983,7 @@ static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, doub
       const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
       const Gm g = {LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, LT_piece,
                     LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, LT_piece,
-                    M, N, P.Kj, G, M, false, SC(0), SC(0)};
+                    M, N, P.Kj, G, M, false, SC(0), SC(0), b.diag ? v : 0};  // diagonal block: pairs a <= b only
       run_gemms<T>(&g, 1, c);
       k_pack_g<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
           G, M, v, b.a0, b.b0, b.nb, b.diag, P.nt, gp, P.Kvp, g_piece_p, gm, P.Kvm, g_piece_m, minus, SC(3));

@@ -39,6 +39,9 @@ struct GemmOp {
   int pieces = 3;               // mixed path: 3 BF16 pieces or 2 scaled FP16 pieces
   const float* scale_a = nullptr;  // FP16 pieces: device scales of A and B (the output is
   const float* scale_b = nullptr;  // divided by their product), else null
+  int64_t tri = 0;                 // mixed path: > 0 skips output tiles whose rows all lie in blocks of
+                                   // `tri` rows past every column block (only the upper block triangle of a
+                                   // symmetric product is read later); the skipped output is left unwritten
   Status* status = nullptr;
   uint64_t timeout_ns = 2000000000ull;
 };

@@ -114,6 +114,7 @@ struct Prob {
   const float* sb;
   long long ldo;
   int M, N, K, mode;
+  int tri;             // > 0: skip output tiles with every row block above every column block
 };
 struct Probs {
   Prob p[2];
@@ -199,6 +200,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int in_grp = lin - grp * RASTER_GROUP * np_n;
   const int m0 = (gm0 + in_grp % gsz) * BM;
   const int n0 = ((in_grp / gsz) * CLUSTER + crank) * BN;
+  if (pr.tri > 0) {
+    // rows and columns come in blocks of pr.tri (a symmetric product's pair index): a cluster whose
+    // smallest row block lies past its largest column block computes nothing anybody reads
+    const int n_end = min(pr.N, ((in_grp / gsz) * CLUSTER + CLUSTER) * BN);
+    if (m0 / pr.tri > (n_end - 1) / pr.tri) return;  // uniform across the cluster
+  }
   const uint16_t cmask = static_cast<uint16_t>((1u << CLUSTER) - 1u);
 
   extern __shared__ uint8_t smem_raw[];
@@ -457,6 +464,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     P.p[i].N = static_cast<int>(op.N);
     P.p[i].K = static_cast<int>(op.K);
     P.p[i].mode = op.mode;
+    P.p[i].tri = static_cast<int>(op.tri);
     const int64_t ngrp = ((op.N + BN - 1) / BN + CLUSTER - 1) / CLUSTER;
     tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ngrp * CLUSTER);
   }
