@@ -45,7 +45,7 @@ PREC = {
 # DRAM bytes of the contraction kernel per step (sum of dram__bytes_read.sum + dram__bytes_write.sum over its
 # launches of one step) from one-pass ncu captures of this kernel version; null for combinations not captured
 TRAFFIC = {
-    ("retinal", "mixed"): (2.424e13, "profiles/cc_gemm_split3_tc_retinal_o78_v650_nj4000_dram_bytes.md"),
+    ("retinal", "mixed"): (2.511e13, "profiles/cc_gemm_split3_tc_retinal_o78_v650_nj4000_dram_bytes.md"),
 }
 
 
