@@ -46,6 +46,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -468,14 +469,18 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     const int64_t ngrp = ((op.N + BN - 1) / BN + CLUSTER - 1) / CLUSTER;
     tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ngrp * CLUSTER);
   }
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
-  if (attr_err != cudaSuccess) {
-    note_cuda(attr_err);
-    return -4;
+  // the shared-memory opt-in is a per-device function attribute: set it once for every device used
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -4;
+  if (!(attr_set.load() & (1ull << dev))) {
+    const cudaError_t attr_err =
+        cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (attr_err != cudaSuccess) {
+      note_cuda(attr_err);
+      return -4;
+    }
+    attr_set.fetch_or(1ull << dev);
   }
   if (tiles > 2147483647LL) return -1;
   cudaLaunchConfig_t cfg;
