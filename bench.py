@@ -386,7 +386,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": PREC[args.prec][1],
-            "data": "synthetic (seeded, device generator; recipe in DESIGN.md)",
+            "data": "synthetic (seeded device generator: MP2 amplitudes from random symmetric Cholesky vectors)",
             "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "global_batch": world,
                        "parallelism": f"independent systems, one per GPU ({world})",
                        "l2": "inputs larger than L2 (55 GB resident), no flush needed",
