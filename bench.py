@@ -45,7 +45,8 @@ PREC = {
 # DRAM bytes of the contraction kernel per step (sum of dram__bytes_read.sum + dram__bytes_write.sum over its
 # launches of one step) from one-pass ncu captures of this kernel version; null for combinations not captured
 TRAFFIC = {
-    ("retinal", "mixed"): (2.511e13, "profiles/cc_gemm_split3_tc_retinal_o78_v650_nj4000_dram_bytes.md"),
+    ("retinal", "mixed"): (2.511e13, "dram__bytes_read.sum + dram__bytes_write.sum over the 420 launches of one "
+                                     "retinal-scale step, kernel with triangle-skipping g-build"),
 }
 
 
@@ -298,8 +299,7 @@ def run_ours(args):
     traffic, traffic_src = TRAFFIC.get((args.workload, args.prec), (None, None))
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_useful, "unit": "TFLOP/s",
                 "frac": achieved / peak_useful, "traffic": traffic,
-                "traffic_basis": ("DRAM bytes per step, all contraction launches of one step (ncu, one pass): "
-                                  + traffic_src) if traffic_src else None,
+                "traffic_basis": ("DRAM bytes per step (ncu, one pass): " + traffic_src) if traffic_src else None,
                 "kernel": "cc_gemm_split3_tc" if args.prec != "fp64" else "cc_gemm_f64_dmma",
                 "peak_basis": basis,
                 "kernel_share_of_step": gemm_ms_step / ms,
