@@ -17,7 +17,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["t_tilde", "density_abic_gs", "w_from_abic", "w_ov3_gs"]
+__all__ = ["t_tilde", "density_abic_gs", "w_from_abic", "w_ov3_gs", "density_abci_es", "w_from_abci",
+           "w_ov3_es_abci"]
 
 
 def t_tilde(t2):
@@ -45,3 +46,27 @@ def w_ov3_gs(tbar1, t2, R0, L_vv, L_ov):
     Om = np.einsum("ma,Kab->Kbm", tbar1, L_vv)         # O^K_bm
     W_ov = R0 * np.einsum("imcb,Kbm->Kic", tt, Om)
     return W_vv, W_ov
+
+
+# --------------------------------------------------------------------------
+# excited state, the d_abci block (App. A): d^es_abci = L_ji^ac R_j^b
+# --------------------------------------------------------------------------
+def density_abci_es(L2, R1):
+    """d[a, b, c, i] = sum_j L_ji^ac R_j^b (L2[j, i, a, c] = L_ji^ac, R1[j, b] = R_j^b)."""
+    return np.einsum("jiac,jb->abci", np.asarray(L2, dtype=np.float64), np.asarray(R1, dtype=np.float64))
+
+
+def w_from_abci(d, L_vv, L_ov):
+    """(W_vv[K, a, b], W_vo[K, i, c]) = (sum_ci d_abci L^K_ci, sum_ab d_abci L^K_ab), L_ci = L_ov[K, i, c]."""
+    return np.einsum("abci,Kic->Kab", d, L_ov), np.einsum("abci,Kab->Kic", d, L_vv)
+
+
+def w_ov3_es_abci(L2, R1, L_vv, L_ov):
+    """The factorised form of Sec. II.C: W_ab^K = R_j^b X^K_aj with X^K_aj = L_ji^ac Z^K_ci, and
+    W_ci^K = L_ji^ac P^K_aj with P^K_aj = R_j^b Z^K_ab (Table I), L^K in place of Z^K."""
+    L2 = np.asarray(L2, dtype=np.float64)
+    X = np.einsum("jiac,Kic->Kaj", L2, L_ov)
+    W_vv = np.einsum("jb,Kaj->Kab", R1, X)
+    P = np.einsum("jb,Kab->Kaj", R1, L_vv)
+    W_vo = np.einsum("jiac,Kaj->Kic", L2, P)
+    return W_vv, W_vo

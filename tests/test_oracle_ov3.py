@@ -55,3 +55,33 @@ def test_t_tilde_matrix_is_symmetric_for_pair_symmetric_t2():
     M = tt.transpose(0, 2, 1, 3).reshape(o * v, o * v)   # rows (i,c), cols (m,b)
     assert np.allclose(M, M.T, rtol=0, atol=1e-15)
     assert rel(V.t_tilde(s.t2)[0, 1], 2 * s.t2[0, 1] - s.t2[1, 0]) < 1e-16
+
+
+def test_es_abci_explicit_matches_factorised_and_fd():
+    s, tb1, L2 = V_case_es()
+    R1 = np.random.default_rng(8).standard_normal(s.t1.shape)
+    d = V.density_abci_es(L2, R1)
+    We, Wo = V.w_from_abci(d, s.L_vv, s.L_ov)
+    Fe, Fo = V.w_ov3_es_abci(L2, R1, s.L_vv, s.L_ov)
+    assert rel(Fe, We) < 1e-14 and rel(Fo, Wo) < 1e-14
+
+    def energy(Lvv, Lov):
+        return float(np.einsum("abci,Kab,Kic->", d, Lvv, Lov))
+
+    h = 1e-6
+    for (K, a, b) in [(0, 2, 5), (2, 6, 1)]:
+        Lp = s.L_vv.copy(); Lp[K, a, b] += h
+        Lm = s.L_vv.copy(); Lm[K, a, b] -= h
+        fd = (energy(Lp, s.L_ov) - energy(Lm, s.L_ov)) / (2 * h)
+        assert abs(fd - Fe[K, a, b]) < 1e-7 * max(1.0, abs(fd))
+    for (K, i, c) in [(1, 1, 4), (3, 2, 0)]:
+        Lp = s.L_ov.copy(); Lp[K, i, c] += h
+        Lm = s.L_ov.copy(); Lm[K, i, c] -= h
+        fd = (energy(s.L_vv, Lp) - energy(s.L_vv, Lm)) / (2 * h)
+        assert abs(fd - Fo[K, i, c]) < 1e-7 * max(1.0, abs(fd))
+
+
+def V_case_es():
+    # a pair-symmetric L2 (left doubles) from the generator's second system
+    s, tb1, tb2 = synth.make_pair(3, 7, 5, 4.0, seed=9)
+    return s, tb1, tb2
