@@ -193,6 +193,19 @@ int cc_ladder_ov3_gs(int32_t o, int32_t v, int32_t nj, const double* L_vv, const
                      const double* t2, const double* tbar1, double R0, double* W_vv,
                      double* W_ov, cc_precision p, void* ws, size_t ws_bytes, void* stream);
 
+/* Excited-state d_abci block (App. A: d^es_abci = L_ji^ac R_j^b) and its
+ * contributions to the three-index intermediates (Sec. II.C, Table I), again
+ * without the OV^3 array and with L^K in place of Z^K:
+ *     W_vv[K][a][b] = sum_j R_j^b X^K_aj,   X^K_aj = sum_ic L_ji^ac L^K_ic
+ *     W_vo[K][i][c] = W_ci^K = sum_aj L_ji^ac P^K_aj,   P^K_aj = sum_b R_j^b L^K_ab
+ * L2 [o][o][v][v] holds the left doubles (L_ij^ab at ((i*o + j)*v + a)*v + b,
+ * pair symmetric); R1 [o][v] the right singles (R_j^b at j*v + b).  Outputs
+ * overwritten.  Precision, workspace (cc_ladder_ov3_workspace_size) and
+ * arithmetic as for cc_ladder_ov3_gs. */
+int cc_ladder_ov3_es_abci(int32_t o, int32_t v, int32_t nj, const double* L_vv, const double* L_ov,
+                          const double* L2, const double* R1, double* W_vv, double* W_vo,
+                          cc_precision p, void* ws, size_t ws_bytes, void* stream);
+
 /* MP2-like driver of the doubles equations from the occupied-virtual block
  * of the Cholesky vectors (Sec. II.A):
  *     g[i][j][a][b] = g_aibj = sum_J L^J_ia L^J_jb      (t2 layout, [o][o][v][v])

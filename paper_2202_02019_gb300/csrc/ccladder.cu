@@ -451,11 +451,12 @@ __global__ void k_jacobi(const double* __restrict__ g, const double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// t~ matrix for the OV^3 contributions: P[(i,c)][(m,b)] = 2 t_im^cb - t_mi^cb
-// (zero for columns past o v), split into the operand format
+// Doubles as an (o v) x (o v) matrix for the OV^3 contributions:
+// P[(i,c)][(m,b)] = alpha x_im^cb + beta x_mi^cb (zero for columns past o v), split into
+// the operand format; (alpha, beta) = (2, -1) gives t~ = 2 t - t^T, (1, 0) the amplitudes
 template <typename T>
-__global__ void k_pack_ttilde(const double* __restrict__ t2, int o, int v, T* __restrict__ P, int64_t ld,
-                              int64_t piece) {
+__global__ void k_pack_pairmat(const double* __restrict__ t2, int o, int v, double alpha, double beta,
+                               T* __restrict__ P, int64_t ld, int64_t piece) {
   const int64_t ov = static_cast<int64_t>(o) * v, vv = static_cast<int64_t>(v) * v;
   const int64_t r = blockIdx.x;  // (i, c)
   const int i = static_cast<int>(r / v), c = static_cast<int>(r % v);
@@ -463,8 +464,8 @@ __global__ void k_pack_ttilde(const double* __restrict__ t2, int o, int v, T* __
     double x = 0.0;
     if (k < ov) {
       const int m = static_cast<int>(k / v), b = static_cast<int>(k % v);
-      x = 2.0 * t2[(static_cast<int64_t>(i) * o + m) * vv + static_cast<int64_t>(c) * v + b] -
-          t2[(static_cast<int64_t>(m) * o + i) * vv + static_cast<int64_t>(c) * v + b];
+      x = alpha * t2[(static_cast<int64_t>(i) * o + m) * vv + static_cast<int64_t>(c) * v + b] +
+          beta * t2[(static_cast<int64_t>(m) * o + i) * vv + static_cast<int64_t>(c) * v + b];
     }
     Store<T>::put(P, r * ld + k, piece, x, 1.f);
   }
@@ -1205,7 +1206,7 @@ static int run_ov3(int o, int v, int nj, const double* L_vv, const double* L_ov,
   const int64_t p_piece = d.ov * d.Kov, b_piece = static_cast<int64_t>(nj) * d.Kov;
   const int64_t nov = static_cast<int64_t>(nj) * d.ov;
   const unsigned grid_e = static_cast<unsigned>(std::min<int64_t>(4096, (nov + 255) / 256));
-  k_pack_ttilde<T><<<static_cast<unsigned>(d.ov), 256, 0, st>>>(t2, o, v, P, d.Kov, p_piece);
+  k_pack_pairmat<T><<<static_cast<unsigned>(d.ov), 256, 0, st>>>(t2, o, v, 2.0, -1.0, P, d.Kov, p_piece);
   k_pack_rows<T><<<4096, 256, 0, st>>>(L_ov, nj, d.ov, B, d.Kov, b_piece);
   c.launched(2);
   const Gm g1 = {P, d.Kov, d.ov, d.Kov, p_piece, B, d.Kov, nj, d.Kov, b_piece, d.ov, nj, d.Kov, G, d.ov, false};
@@ -1213,11 +1214,10 @@ static int run_ov3(int o, int v, int nj, const double* L_vv, const double* L_ov,
   k_to_f64_scaled<S><<<grid_e, 256, 0, st>>>(G, Y, nov, 1.0);
   c.launched();
   // W_vv[K][a][b] = R0 sum_m tbar1[m][a] Y[K][m][b]
-  c.check(batched_gemm_f64(v, v, o, nj, tbar1, 1, v, Y, d.ov, v, nullptr, 0, 0, R0, W_vv,
-                           static_cast<int64_t>(v) * v, v, st));
+  const int64_t vv = static_cast<int64_t>(v) * v;
+  c.check(batched_gemm_f64({v, v, o, nj, tbar1, 1, v, Y, d.ov, v, 1, nullptr, 0, 0, 0, R0, W_vv, vv, v, 1}, st));
   // O[K][m][b] = sum_a tbar1[m][a] L_vv[K][a][b]   (into Y, whose contents are used up)
-  c.check(batched_gemm_f64(o, v, v, nj, tbar1, v, 1, L_vv, static_cast<int64_t>(v) * v, v, nullptr, 0, 0, 1.0, Y,
-                           d.ov, v, st));
+  c.check(batched_gemm_f64({o, v, v, nj, tbar1, v, 1, L_vv, vv, v, 1, nullptr, 0, 0, 0, 1.0, Y, d.ov, v, 1}, st));
   k_pack_rows<T><<<4096, 256, 0, st>>>(Y, nj, d.ov, B, d.Kov, b_piece);
   c.launched();
   const Gm g2 = {P, d.Kov, d.ov, d.Kov, p_piece, B, d.Kov, nj, d.Kov, b_piece, d.ov, nj, d.Kov, G, d.ov, false};
@@ -1227,11 +1227,70 @@ static int run_ov3(int o, int v, int nj, const double* L_vv, const double* L_ov,
   return c.err;
 }
 
+// Excited state, the d_abci block: d_abci = L_ji^ac R_j^b.
+//   X^K_aj = sum_ic L_ji^ac L^K_ic,  W_ab^K = sum_j R_j^b X^K_aj
+//   P^K_aj = sum_b R_j^b L^K_ab,     W_ci^K = sum_aj L_ji^ac P^K_aj
+// The matrix Q[(j,a)][(i,c)] = L_ji^ac is symmetric for pair-symmetric L2 and
+// is the A operand of both (o v) x N_J contractions, as t~ is in the ground state.
+template <typename T>
+static int run_ov3_es_abci(int o, int v, int nj, const double* L_vv, const double* L_ov, const double* L2,
+                           const double* R1, double* W_vv, double* W_vo, const Ov3Plan& d, char* ws,
+                           cudaStream_t st) {
+  using S = typename Path<T>::S;
+  Ctx c;
+  c.st = st;
+  c.status = reinterpret_cast<Status*>(ws);
+  c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
+  c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
+  T* P = at<T>(ws, d.o_P);
+  T* B = at<T>(ws, d.o_B);
+  S* G = at<S>(ws, d.o_G);
+  double* X = at<double>(ws, d.o_Y);
+  const int64_t p_piece = d.ov * d.Kov, b_piece = static_cast<int64_t>(nj) * d.Kov;
+  const int64_t nov = static_cast<int64_t>(nj) * d.ov, vv = static_cast<int64_t>(v) * v;
+  const unsigned grid_e = static_cast<unsigned>(std::min<int64_t>(4096, (nov + 255) / 256));
+  k_pack_pairmat<T><<<static_cast<unsigned>(d.ov), 256, 0, st>>>(L2, o, v, 1.0, 0.0, P, d.Kov, p_piece);
+  k_pack_rows<T><<<4096, 256, 0, st>>>(L_ov, nj, d.ov, B, d.Kov, b_piece);
+  c.launched(2);
+  const Gm g1 = {P, d.Kov, d.ov, d.Kov, p_piece, B, d.Kov, nj, d.Kov, b_piece, d.ov, nj, d.Kov, G, d.ov, false};
+  run_gemms<T>(&g1, 1, c);  // G[K][(j,a)] = X^K_aj
+  k_to_f64_scaled<S><<<grid_e, 256, 0, st>>>(G, X, nov, 1.0);
+  c.launched();
+  // W_vv[K][a][b] = sum_j R1[j][b] X[K][j][a]: rows b, columns a, stored transposed
+  c.check(batched_gemm_f64({v, v, o, nj, R1, 1, v, X, d.ov, v, 1, nullptr, 0, 0, 0, 1.0, W_vv, vv, 1, v}, st));
+  // P[K][j][a] = sum_b R1[j][b] L_vv[K][a][b]   (into X, whose contents are used up)
+  c.check(batched_gemm_f64({o, v, v, nj, R1, v, 1, L_vv, vv, 1, v, nullptr, 0, 0, 0, 1.0, X, d.ov, v, 1}, st));
+  k_pack_rows<T><<<4096, 256, 0, st>>>(X, nj, d.ov, B, d.Kov, b_piece);
+  c.launched();
+  const Gm g2 = {P, d.Kov, d.ov, d.Kov, p_piece, B, d.Kov, nj, d.Kov, b_piece, d.ov, nj, d.Kov, G, d.ov, false};
+  run_gemms<T>(&g2, 1, c);  // G[K][(i,c)] = W_ci^K
+  k_to_f64_scaled<S><<<grid_e, 256, 0, st>>>(G, W_vo, nov, 1.0);
+  c.launched();
+  return c.err;
+}
+
 }  // namespace ccl
 
 using namespace ccl;
 
 extern "C" {
+
+int cc_ladder_ov3_es_abci(int32_t o, int32_t v, int32_t nj, const double* L_vv, const double* L_ov,
+                          const double* L2, const double* R1, double* W_vv, double* W_vo, cc_precision p, void* ws,
+                          size_t ws_bytes, void* stream) {
+  if (o < 1 || v < 1 || nj < 1 || !L_vv || !L_ov || !L2 || !R1 || !W_vv || !W_vo) return CC_ERR_ARG;
+  if (!aligned8(L_vv) || !aligned8(L_ov) || !aligned8(L2) || !aligned8(R1) || !aligned8(W_vv) || !aligned8(W_vo))
+    return CC_ERR_ARG;
+  if (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) return CC_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  if (const int rc = check_device()) return rc;
+  const Ov3Plan d = ov3_plan(o, v, nj, p);
+  if (ws_bytes < d.total) return CC_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p == CC_PREC_FP64)
+    return run_ov3_es_abci<double>(o, v, nj, L_vv, L_ov, L2, R1, W_vv, W_vo, d, static_cast<char*>(ws), st);
+  return run_ov3_es_abci<__nv_bfloat16>(o, v, nj, L_vv, L_ov, L2, R1, W_vv, W_vo, d, static_cast<char*>(ws), st);
+}
 
 size_t cc_ladder_ov3_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p) {
   if (o < 1 || v < 1 || nj < 1 || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2)) return 0;

@@ -50,13 +50,19 @@ struct GemmOp {
 int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream);
 int gemm_f64(const GemmOp& op, cudaStream_t stream);
 
-// C_J = X_J + alpha * A B_J for J < nb, FP64 (csrc/t1.cu): A element (m, k) at
-// m * a_sm + k * a_sk, shared by every J; B_J [K][N], X_J and C_J [M][N]
-// row-major with leading dimensions ldb, ldx, ldc and J strides b_sj, x_sj,
-// c_sj; X may be null.  Returns 0 or CC_ERR_CUDA.
-int batched_gemm_f64(int M, int N, int K, int nb, const double* A, int64_t a_sm, int64_t a_sk, const double* B,
-                     int64_t b_sj, int64_t ldb, const double* X, int64_t x_sj, int64_t ldx, double alpha, double* C,
-                     int64_t c_sj, int64_t ldc, cudaStream_t st);
+// C_J = X_J + alpha * A B_J for J < nb, FP64 (csrc/t1.cu).  Element (m, k) of
+// A (shared by every J) is at m * a_sm + k * a_sk; element (k, n) of B_J at
+// J * b_sj + k * b_sk + n * b_sn; (m, n) of X_J and C_J likewise with their
+// strides.  X may be null.  Returns 0 or CC_ERR_CUDA.
+struct BatchedF64 {
+  int M, N, K, nb;
+  const double* A; int64_t a_sm, a_sk;
+  const double* B; int64_t b_sj, b_sk, b_sn;
+  const double* X; int64_t x_sj, x_sm, x_sn;
+  double alpha;
+  double* C; int64_t c_sj, c_sm, c_sn;
+};
+int batched_gemm_f64(const BatchedF64& g, cudaStream_t st);
 
 // Records the text of a failed CUDA call for cc_ladder_strerror.
 void note_cuda(cudaError_t e);

@@ -24,22 +24,20 @@ namespace {
 
 constexpr int TM = 32, TN = 64, TK = 32, NT = 256;
 
-// C_J[m][n] = X_J[m][n] + alpha * sum_k A[m][k] B_J[k][n] for J < nb.
-// A is shared by every J (element (m, k) at m * a_sm + k * a_sk); B_J, X_J and
-// C_J are row-major with leading dimensions ldb, ldx, ldc and J strides
-// b_sj, x_sj, c_sj.  X may be null (treated as zero).
-__global__ void __launch_bounds__(NT) k_batched_gemm_f64(int M, int N, int K, int nb, const double* __restrict__ A,
-                                                         int64_t a_sm, int64_t a_sk, const double* __restrict__ B,
-                                                         int64_t b_sj, int64_t ldb, const double* __restrict__ X,
-                                                         int64_t x_sj, int64_t ldx, double alpha,
-                                                         double* __restrict__ C, int64_t c_sj, int64_t ldc) {
+// C_J[m][n] = X_J[m][n] + alpha * sum_k A[m][k] B_J[k][n] for J < nb, every
+// operand addressed by element strides (see BatchedF64).  X may be null.
+__global__ void __launch_bounds__(NT) k_batched_gemm_f64(const BatchedF64 g) {
+  const int M = g.M, N = g.N, K = g.K, nb = g.nb;
+  const double* __restrict__ A = g.A;
+  const double* __restrict__ B = g.B;
   __shared__ double As[TK][TM + 1];
   __shared__ double Bs[TK][TN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  const bool a_k_contig = (a_sk == 1);
+  const bool a_k_contig = (g.a_sk == 1);
+  const bool b_k_contig = (g.b_sk == 1 && g.b_sn != 1);
   for (int J = blockIdx.z; J < nb; J += gridDim.z) {
-    const double* BJ = B + static_cast<int64_t>(J) * b_sj;
+    const double* BJ = B + static_cast<int64_t>(J) * g.b_sj;
     double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
     for (int k0 = 0; k0 < K; k0 += TK) {
 #pragma unroll
@@ -48,14 +46,15 @@ __global__ void __launch_bounds__(NT) k_batched_gemm_f64(int M, int N, int K, in
         const int mm = a_k_contig ? idx / TK : idx % TM;
         const int kk = a_k_contig ? idx % TK : idx / TM;
         const int m = m0 + mm, k = k0 + kk;
-        As[kk][mm] = (m < M && k < K) ? A[static_cast<int64_t>(m) * a_sm + static_cast<int64_t>(k) * a_sk] : 0.0;
+        As[kk][mm] = (m < M && k < K) ? A[static_cast<int64_t>(m) * g.a_sm + static_cast<int64_t>(k) * g.a_sk] : 0.0;
       }
 #pragma unroll
       for (int r = 0; r < (TK * TN) / NT; ++r) {
         const int idx = tid + r * NT;
-        const int nn = idx % TN, kk = idx / TN;
+        const int nn = b_k_contig ? idx / TK : idx % TN;
+        const int kk = b_k_contig ? idx % TK : idx / TN;
         const int n = n0 + nn, k = k0 + kk;
-        Bs[kk][nn] = (n < N && k < K) ? BJ[static_cast<int64_t>(k) * ldb + n] : 0.0;
+        Bs[kk][nn] = (n < N && k < K) ? BJ[static_cast<int64_t>(k) * g.b_sk + static_cast<int64_t>(n) * g.b_sn] : 0.0;
       }
       __syncthreads();
 #pragma unroll 8
@@ -78,8 +77,11 @@ __global__ void __launch_bounds__(NT) k_batched_gemm_f64(int M, int N, int K, in
       for (int j = 0; j < 4; ++j) {
         const int n = n0 + tx + 16 * j;
         if (n >= N) continue;
-        const double x = X ? X[static_cast<int64_t>(J) * x_sj + static_cast<int64_t>(m) * ldx + n] : 0.0;
-        C[static_cast<int64_t>(J) * c_sj + static_cast<int64_t>(m) * ldc + n] = fma(alpha, acc[i][j], x);
+        const double x =
+            g.X ? g.X[static_cast<int64_t>(J) * g.x_sj + static_cast<int64_t>(m) * g.x_sm + static_cast<int64_t>(n) * g.x_sn]
+                : 0.0;
+        g.C[static_cast<int64_t>(J) * g.c_sj + static_cast<int64_t>(m) * g.c_sm + static_cast<int64_t>(n) * g.c_sn] =
+            fma(g.alpha, acc[i][j], x);
       }
     }
   }
@@ -100,12 +102,9 @@ bool overlap(const double* p, int64_t n, const double* q, int64_t m) { return p 
 
 }  // namespace
 
-int batched_gemm_f64(int M, int N, int K, int nb, const double* A, int64_t a_sm, int64_t a_sk, const double* B,
-                     int64_t b_sj, int64_t ldb, const double* X, int64_t x_sj, int64_t ldx, double alpha, double* C,
-                     int64_t c_sj, int64_t ldc, cudaStream_t st) {
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, nb < 65535 ? nb : 65535);
-  k_batched_gemm_f64<<<grid, NT, 0, st>>>(M, N, K, nb, A, a_sm, a_sk, B, b_sj, ldb, X, x_sj, ldx, alpha, C, c_sj,
-                                          ldc);
+int batched_gemm_f64(const BatchedF64& g, cudaStream_t st) {
+  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.nb < 65535 ? g.nb : 65535);
+  k_batched_gemm_f64<<<grid, NT, 0, st>>>(g);
   count_launch();
   const cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) {
@@ -131,9 +130,9 @@ int cc_ladder_t1_transform(int32_t o, int32_t v, int32_t nj, const double* L_vv,
     return CC_ERR_ARG;
   if (const int rc = device_ok()) return rc;
   // M = a (v), N = c (v), K = i (o): A[a][i] = t1[i][a], B_J[i][c] = L_ov[J][i][c]
-  return batched_gemm_f64(v, v, o, nj, t1, 1, v, L_ov, static_cast<int64_t>(o) * v, v, L_vv,
-                          static_cast<int64_t>(v) * v, v, -1.0, L_vv_t1, static_cast<int64_t>(v) * v, v,
-                          static_cast<cudaStream_t>(stream));
+  const int64_t vv = static_cast<int64_t>(v) * v;
+  BatchedF64 g{v, v, o, nj, t1, 1, v, L_ov, static_cast<int64_t>(o) * v, v, 1, L_vv, vv, v, 1, -1.0, L_vv_t1, vv, v, 1};
+  return batched_gemm_f64(g, static_cast<cudaStream_t>(stream));
 }
 
 int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_vv, const double* t1, double* W_ov,
@@ -144,8 +143,9 @@ int cc_ladder_w_backtransform(int32_t o, int32_t v, int32_t nj, const double* W_
   if (overlap(W_ov, nov, W_vv, nvv) || overlap(W_ov, nov, t1, static_cast<int64_t>(o) * v)) return CC_ERR_ARG;
   if (const int rc = device_ok()) return rc;
   // M = i (o), N = c (v), K = a (v): A[i][a] = t1[i][a], B_J[a][c] = W_vv[J][a][c]
-  return batched_gemm_f64(o, v, v, nj, t1, v, 1, W_vv, static_cast<int64_t>(v) * v, v, nullptr, 0, 0, -1.0, W_ov,
-                          static_cast<int64_t>(o) * v, v, static_cast<cudaStream_t>(stream));
+  BatchedF64 g{o, v, v, nj, t1, v, 1, W_vv, static_cast<int64_t>(v) * v, v, 1, nullptr, 0, 0, 0, -1.0, W_ov,
+               static_cast<int64_t>(o) * v, v, 1};
+  return batched_gemm_f64(g, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

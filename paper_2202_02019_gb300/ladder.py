@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_ov3_workspace_size.restype = S
     lib.cc_ladder_ov3_gs.argtypes = [I, I, I, P, P, P, P, ctypes.c_double, P, P, I, VP, S, VP]
     lib.cc_ladder_ov3_gs.restype = I
+    lib.cc_ladder_ov3_es_abci.argtypes = [I, I, I, P, P, P, P, P, P, I, VP, S, VP]
+    lib.cc_ladder_ov3_es_abci.restype = I
     lib.cc_ladder_set_tuning.argtypes = [I, I]
     lib.cc_ladder_set_tuning.restype = I
     lib.cc_ladder_profile.argtypes = [I]
@@ -108,7 +110,7 @@ EXPORTS = (
     "cc_ladder_residual_adjoint", "cc_ladder_set_tuning", "cc_ladder_t1_transform",
     "cc_ladder_w_backtransform", "cc_ladder_density_es", "cc_ladder_mp2_driver_workspace_size",
     "cc_ladder_mp2_driver", "cc_ladder_iterate_workspace_size", "cc_ladder_iterate",
-    "cc_ladder_ov3_workspace_size", "cc_ladder_ov3_gs",
+    "cc_ladder_ov3_workspace_size", "cc_ladder_ov3_gs", "cc_ladder_ov3_es_abci",
 )
 
 
@@ -371,6 +373,23 @@ def cc_ladder_ov3_gs(L_vv, L_ov, t2, tbar1, R0=1.0, prec="mixed", ws=None, strea
                                 _f64(tbar1, "tbar1"), float(R0), _f64(W_vv, "W_vv"), _f64(W_ov, "W_ov"),
                                 _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return W_vv, W_ov
+
+
+def cc_ladder_ov3_es_abci(L_vv, L_ov, L2, R1, prec="mixed", ws=None, stream=None):
+    """Excited-state d_abci contributions (W_vv [nj, v, v], W_vo [nj, o, v] = W_ci)."""
+    lib = load()
+    nj, o, v = L_ov.shape
+    if ws is None:
+        n = int(lib.cc_ladder_ov3_workspace_size(o, v, nj, _prec(prec)))
+        if n == 0:
+            raise LadderError(-1, "invalid sizes for the OV^3 workspace")
+        ws = torch.empty(n, dtype=torch.uint8, device=L_vv.device)
+    W_vv = torch.empty_like(L_vv)
+    W_vo = torch.empty_like(L_ov)
+    _check(lib.cc_ladder_ov3_es_abci(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(L2, "L2"),
+                                     _f64(R1, "R1"), _f64(W_vv, "W_vv"), _f64(W_vo, "W_vo"), _prec(prec),
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return W_vv, W_vo
 
 
 def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):

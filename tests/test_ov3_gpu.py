@@ -33,3 +33,15 @@ def test_ov3_contributions_match_oracle(o, v, nj, prec):
     W_vv, W_ov = lad.cc_ladder_ov3_gs(dev(s.L_vv), dev(s.L_ov), dev(s.t2), dev(tb1), R0, prec=prec)
     assert rel(W_vv.cpu(), ref_vv) < TOL[prec]
     assert rel(W_ov.cpu(), ref_ov) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("o,v,nj", [(3, 7, 5), (5, 37, 70), (8, 48, 160)])
+def test_es_abci_contributions_match_oracle(o, v, nj, prec):
+    s, _, L2 = synth.make_pair(o, v, nj, nj / 6.0, seed=2203)
+    R1 = np.random.default_rng(o + v).standard_normal((o, v))
+    d = V.density_abci_es(L2, R1)
+    ref_vv, ref_vo = V.w_from_abci(d, s.L_vv, s.L_ov)
+    W_vv, W_vo = lad.cc_ladder_ov3_es_abci(dev(s.L_vv), dev(s.L_ov), dev(L2), dev(R1), prec=prec)
+    assert rel(W_vv.cpu(), ref_vv) < TOL[prec]
+    assert rel(W_vo.cpu(), ref_vo) < TOL[prec]
