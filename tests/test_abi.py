@@ -93,3 +93,29 @@ def test_t1_entry_points_host_checks():
     assert lib.cc_ladder_t1_transform(2, 5, 3, *good, P(0x10000 + 8), None) == -1      # output overlaps L_vv
     assert lib.cc_ladder_w_backtransform(2, 5, 0, good[0], good[1], P(0x40000), None) == -1
     assert lib.cc_ladder_w_backtransform(2, 5, 3, good[0], good[1], P(0x20000), None) == -1  # overlaps t1
+
+
+def test_workspace_queries_and_argument_errors_of_the_extra_entry_points():
+    # host-side checks only: sizes, NULLs and alignment are rejected before any device work
+    lib = lad.load()
+    P = ctypes.c_void_p
+    assert lib.cc_ladder_mp2_driver_workspace_size(0, 5, 3, 1) == 0
+    assert lib.cc_ladder_mp2_driver_workspace_size(2, 5, 3, 9) == 0
+    assert lib.cc_ladder_mp2_driver_workspace_size(2, 5, 3, 0) > lib.cc_ladder_mp2_driver_workspace_size(2, 5, 3, 1) > 0
+    assert lib.cc_ladder_ov3_workspace_size(2, 5, 3, 1) > 0 and lib.cc_ladder_ov3_workspace_size(2, 0, 3, 1) == 0
+    ws = P(0x100000)
+    assert lib.cc_ladder_mp2_driver(2, 5, 3, None, P(0x2000), 1, ws, 1 << 30, None) == -1
+    assert lib.cc_ladder_mp2_driver(2, 5, 3, P(0x1000), P(0x2004), 1, ws, 1 << 30, None) == -1
+    assert lib.cc_ladder_mp2_driver(2, 5, 3, P(0x1000), P(0x2000), 1, P(0x100008), 1 << 30, None) == -1
+    assert lib.cc_ladder_ov3_gs(2, 5, 3, P(0x1000), P(0x2000), None, P(0x3000), ctypes.c_double(1.0),
+                                P(0x4000), P(0x5000), 1, ws, 1 << 30, None) == -1
+    assert lib.cc_ladder_ov3_es_abci(2, 5, 3, P(0x1000), P(0x2000), P(0x3000), P(0x3800), P(0x4000), None, 1,
+                                     ws, 1 << 30, None) == -1
+    arr = (lad.cc_ladder_system * 1)(fake_sys(2, 5, 3))
+    assert lib.cc_ladder_iterate_workspace_size(arr, 1) > 0
+    # eps is required by the iteration, and at least one step
+    no_eps = (lad.cc_ladder_system * 1)(lad.cc_ladder_system(2, 5, 3, 0x1000, 0x2000, 0x3000, 0x4000, 0))
+    assert lib.cc_ladder_iterate(no_eps, P(0x7000), 2, P(0x8000), P(0x9000), 1, ws, 1 << 30, None) == -1
+    assert lib.cc_ladder_iterate(arr, P(0x7000), 0, P(0x8000), P(0x9000), 1, ws, 1 << 30, None) == -1
+    assert lib.cc_ladder_density_es(arr, 1, None, (ctypes.c_double * 1)(1.0), (P * 1)(0x6000), 1, ws, 1 << 30,
+                                    None) == -1
