@@ -16,7 +16,7 @@ from paper_2202_02019_gb300.autograd import ladder_energy
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-11, "mixed": 1e-6}
+TOL = {"fp64": 1e-11, "mixed": 1e-6, "fp16x2": 1e-6}
 
 
 def rel(a, b):
@@ -43,7 +43,7 @@ def _grads(s, tt, tb2, prec):
     return float(E.detach()), L.grad.cpu().numpy(), tau.grad.cpu().numpy(), tbar.grad.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp16x2"])
 def test_gradients_match_oracle(fd_case, prec):
     s, tt, tb2 = fd_case
     E, gL, gT, gB = _grads(s, tt, tb2, prec)
