@@ -45,7 +45,7 @@ PREC = {
 # DRAM bytes of the contraction kernel per step (sum of dram__bytes_read.sum + dram__bytes_write.sum over its
 # launches of one step) from one-pass ncu captures of this kernel version; null for combinations not captured
 TRAFFIC = {
-    ("retinal", "mixed"): (2.511e13, "dram__bytes_read.sum + dram__bytes_write.sum over the 420 launches of one "
+    ("retinal", "mixed"): (2.465e13, "dram__bytes_read.sum + dram__bytes_write.sum over the 420 launches of one "
                                      "retinal-scale step, kernel with triangle-skipping g-build"),
 }
 

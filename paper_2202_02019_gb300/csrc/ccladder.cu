@@ -350,19 +350,30 @@ __global__ void k_unpack_gamma(const S* __restrict__ Gp, const S* __restrict__ G
       dst = bot; ld = ldb; piece = bpiece;
       xrow = static_cast<int64_t>(bl) * v; ycol = static_cast<int64_t>(al) * vp;
     }
-    // the tile itself (rows in ct, cols in dt) and, off the diagonal, its mirror
+    // the tile itself (rows in ct, cols in dt) and, off the diagonal, its mirror; each thread
+    // writes two adjacent columns (an even slab offset: ld, ycol and the tile origin are even)
+    const int cp = (ty * 32 + tx) & 15, rr = (ty * 32 + tx) >> 4;
     for (int mirror = 0; mirror < (ct == dt ? 1 : 2); ++mirror) {
       const int R0 = mirror ? d0 : c0, W0 = mirror ? c0 : d0;
-      for (int r = ty; r < 32; r += 8) {
-        const int row = R0 + r, col = W0 + tx;
+      for (int r = rr; r < 32; r += 16) {
+        const int row = R0 + r, col = W0 + 2 * cp;
         if (row >= v || col >= v) continue;
-        const int lo = min(row, col), hi = max(row, col);
-        const V P = sP[lo - c0][hi - d0];
-        const V M = sM[lo - c0][hi - d0];
-        // sign of M: +1 above the diagonal for (a, b), flipped below it and for (b, a)
-        const bool addM = (row < col) == (which == 0);
-        const V val = (row == col) ? P : (addM ? A::add(P, M) : A::sub(P, M));
-        Put<T, V>::put(dst, (xrow + row) * ld + ycol + col, piece, val, sc);
+        V val[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cl = min(col + h, v - 1);
+          const int lo = min(row, cl), hi = max(row, cl);
+          const V P = sP[lo - c0][hi - d0];
+          const V M = sM[lo - c0][hi - d0];
+          // sign of M: +1 above the diagonal for (a, b), flipped below it and for (b, a)
+          const bool addM = (row < cl) == (which == 0);
+          val[h] = (row == cl) ? P : (addM ? A::add(P, M) : A::sub(P, M));
+        }
+        const int64_t idx = (xrow + row) * ld + ycol + col;
+        if (col + 1 < v)
+          Put2<T, V>::put2(dst, idx, piece, val[0], val[1], sc);
+        else
+          Put<T, V>::put(dst, idx, piece, val[0], sc);
       }
     }
   }

@@ -157,6 +157,46 @@ struct Put<__half, float2> {
   }
 };
 
+// Two adjacent elements at once (idx even, so the 16-bit pieces of the pair
+// form one aligned 32-bit word): the same values as two Put::put calls with
+// half the conversions and stores.
+template <typename T, typename V>
+struct Put2;
+template <>
+struct Put2<double, double> {
+  static __device__ __forceinline__ void put2(double* base, int64_t idx, int64_t, double x0, double x1, float) {
+    base[idx] = x0;
+    base[idx + 1] = x1;
+  }
+};
+template <>
+struct Put2<__nv_bfloat16, float2> {
+  static __device__ __forceinline__ void put2(__nv_bfloat16* base, int64_t idx, int64_t piece, float2 x0, float2 x1,
+                                              float) {
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(x0.x, x1.x);
+    const float2 b0 = __bfloat1622float2(p0);
+    const float r0 = (x0.x - b0.x) + x0.y, r1 = (x1.x - b0.y) + x1.y;
+    const __nv_bfloat162 p1 = __floats2bfloat162_rn(r0, r1);
+    const float2 b1 = __bfloat1622float2(p1);
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(r0 - b1.x, r1 - b1.y);
+    *reinterpret_cast<__nv_bfloat162*>(base + idx) = p0;
+    *reinterpret_cast<__nv_bfloat162*>(base + idx + piece) = p1;
+    *reinterpret_cast<__nv_bfloat162*>(base + idx + 2 * piece) = p2;
+  }
+};
+template <>
+struct Put2<__half, float2> {
+  static __device__ __forceinline__ void put2(__half* base, int64_t idx, int64_t piece, float2 x0, float2 x1,
+                                              float scl) {
+    const float hi0 = x0.x * scl, hi1 = x1.x * scl;
+    const __half2 h0 = __floats2half2_rn(hi0, hi1);
+    const float2 b0 = __half22float2(h0);
+    *reinterpret_cast<__half2*>(base + idx) = h0;
+    *reinterpret_cast<__half2*>(base + idx + piece) =
+        __floats2half2_rn((hi0 - b0.x) + x0.y * scl, (hi1 - b0.y) + x1.y * scl);
+  }
+};
+
 // ---------------------------------------------------------------- pair index
 // Row-major upper triangle of an n x n index square.
 //   symmetric pairs  p <= q : k = p*(2n - p + 1)/2 + (q - p)
