@@ -4,11 +4,12 @@ Tolerances (relative Frobenius error; E: relative error):
   FP64 path   Omega, D <= 1e-11, E <= 1e-11
   mixed paths Omega, D <= 1e-6,  E <= 1e-6  (split-BF16 and scaled split-FP16)
 The FP64 path only reorders FP64 sums (K-chunked DMMA, atomics), so it
-sits near 1e-15.  The mixed path carries 24-bit operands (three BF16
-pieces); the tensor core's FP32 accumulation truncates, so the leading
-piece product is re-started every 64 K terms and summed error-free, which
-leaves a small coherent bias (about -4e-8 per contraction).  E inherits
-that bias from Omega, so it is held to the same 1e-6 as Omega.
+sits near 1e-15.  The split paths carry 24-bit (three BF16 pieces) or 22-bit
+(two scaled FP16 pieces) operands; the tensor core's FP32 accumulation
+truncates, so the leading piece product is re-started every 128 (BF16) or
+64 (FP16) K terms and the window sums are added without drift, which leaves
+a small coherent bias toward zero (2-6e-7 on these cases).  E inherits that
+bias from Omega, so it is held to the same 1e-6 as Omega.
 """
 import numpy as np
 import pytest
