@@ -141,6 +141,8 @@ class System:
                 return None
             if t.dtype != torch.float64 or not t.is_contiguous():
                 raise ValueError("ladder tensors must be contiguous float64")
+            if not t.is_cuda:
+                raise ValueError("ladder tensors must live on the GPU (the kernels read device memory)")
             return t.data_ptr()
         return cc_ladder_system(self.o, self.v, self.nj, ptr(self.L_vv), ptr(self.t1),
                                 ptr(self.t2), ptr(self.tbar2), ptr(self.eps))
@@ -154,6 +156,9 @@ def _arr(systems: Sequence[System]):
 
 
 def _ptrs(ts):
+    for t in ts:
+        if t.dtype != torch.float64 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("output and amplitude buffers must be contiguous float64 GPU tensors")
     return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
 
 
@@ -188,6 +193,8 @@ def workspace(systems: Sequence[System], prec="mixed", which=CC_WS_STEP, device=
 def _ws(systems, prec, which, ws):
     if ws is None:
         ws = workspace(systems, prec, which)
+    if not ws.is_cuda:
+        raise ValueError("the workspace must be GPU memory")
     return ws
 
 
@@ -221,6 +228,11 @@ def cc_ladder_density(systems, prec="mixed", ws=None, out=None, stream=None):
 
 def cc_ladder_density_es(systems, R2, R0, prec="mixed", ws=None, out=None, stream=None):
     """Excited-state density: D with U = R0 * t2 + R2 in place of tau (tbar2 = left doubles L2)."""
+    if len(R2) != len(systems) or len(R0) != len(systems):
+        raise ValueError("one R2 buffer and one R0 value per system")
+    for s_, r in zip(systems, R2):
+        if tuple(r.shape) != tuple(s_.t2.shape):
+            raise ValueError("R2 must have the shape of t2")
     lib = load()
     ws = _ws(systems, prec, CC_WS_DENSITY, ws)
     out = out or [torch.empty_like(s.L_vv) for s in systems]
@@ -305,6 +317,8 @@ def cc_ladder_profile_read():
 def _f64(t, name):
     if t.dtype != torch.float64 or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous float64 tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on the GPU (the kernels read device memory)")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -344,6 +358,8 @@ def cc_ladder_mp2_driver(L_ov, prec="mixed", ws=None, out=None, stream=None):
 
 def cc_ladder_iterate(system, g_drv, n_iter, prec="mixed", ws=None, out=None, dnorm2=None, stream=None):
     """n_iter Jacobi steps of the ladder + driver doubles equations; returns (t2, sum (t' - t)^2 per step)."""
+    if tuple(g_drv.shape) != tuple(system.t2.shape):
+        raise ValueError("the driver must have the shape of t2")
     lib = load()
     arr = _arr([system])
     if ws is None:

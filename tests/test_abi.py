@@ -119,3 +119,17 @@ def test_workspace_queries_and_argument_errors_of_the_extra_entry_points():
     assert lib.cc_ladder_iterate(arr, P(0x7000), 0, P(0x8000), P(0x9000), 1, ws, 1 << 30, None) == -1
     assert lib.cc_ladder_density_es(arr, 1, None, (ctypes.c_double * 1)(1.0), (P * 1)(0x6000), 1, ws, 1 << 30,
                                     None) == -1
+
+
+def test_binding_rejects_host_tensors_before_any_call():
+    # a host pointer handed to the kernels would be read as device memory: the binding refuses it
+    import torch
+    s = lad.System(L_vv=torch.zeros(3, 4, 4, dtype=torch.float64), t2=torch.zeros(2, 2, 4, 4, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        s.c_struct()
+    with pytest.raises(ValueError):
+        lad._ptrs([torch.zeros(4, dtype=torch.float64)])
+    with pytest.raises(ValueError):
+        lad._f64(torch.zeros(4, dtype=torch.float64), "x")
+    with pytest.raises(ValueError):
+        lad.cc_ladder_density_es([s], [], [1.0])
