@@ -250,8 +250,11 @@ int cc_ladder_status(void* ws, void* stream);
  * (64 systems x 1024 doubles = 512 KiB, held on every GPU that loads the
  * library until the process exits).  At most 64 systems per call; more
  * returns CC_ERR_SIZE.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the array and it
+ * device address (cudaGetSymbolAddress) with the device current; under
+ * CUDA's lazy module loading that is also when the driver brings this part of
+ * the library, array included, onto the GPU.  Make that first call before any
+ * stream capture and before relying on the device's free memory staying put;
+ * later calls allocate nothing.  All calls share the array and it
  * keeps the last call's contents (each call overwrites what it reads);
  * calls that overlap on the GPU -- other streams, other host threads on the
  * same device -- race on it and must be serialised by the caller. */

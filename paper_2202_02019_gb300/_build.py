@@ -21,7 +21,7 @@ SOURCES = ["ccladder.cu", "gemm_mixed.cu", "gemm_f64.cu", "noalloc.cu", "t1.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{INC}", f"-I{CSRC}"]
-# optional extra nvcc flags (build options such as -DCC_GEMM_CLUSTER=1)
+# optional extra nvcc flags (extra defines or diagnostics such as -Xptxas -v)
 FLAGS += os.environ.get("CC_NVCC_FLAGS", "").split()
 
 

@@ -39,8 +39,8 @@
 // reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile
 // 128 x 128 x 64 with a 192 KB smem ring (BF16: 2 stages of 3 A + 3 B
 // pieces; FP16: 3 stages of 2 + 2), 128-byte swizzle (128-byte TMA rows move
-// operands ~1.2x faster than 64-byte ones).  Clusters of CLUSTER CTAs take
-// adjacent n-tiles of one m-tile and multicast its A tile.  TMEM columns:
+// operands ~1.2x faster than 64-byte ones).  Every CTA loads its own A and B
+// tiles (one 3-D box of all pieces each).  TMEM columns:
 // H0 [0,128), H1 [128,256), L [256,384), LO [384,512).
 // Every wait is bounded (globaltimer) and latches CC_ERR_TIMEOUT.
 #include <cudaTypedefs.h>
@@ -59,12 +59,7 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int RASTER_GROUP = 8;           // m-tiles per raster group (L2 reuse of B panels)
-#ifndef CC_GEMM_CLUSTER
-#define CC_GEMM_CLUSTER 2
-#endif
-constexpr int CLUSTER = CC_GEMM_CLUSTER;  // CTAs sharing one A tile (TMA multicast); 1 or 2
 constexpr int A_PIECE = BM * BK * 2;      // 16384 B (one 16-bit piece of a 128 x 64 tile)
-constexpr int A_HALF = A_PIECE / CLUSTER; // bytes of one piece's row slice
 constexpr int B_PIECE = BN * BK * 2;      // 16384 B
 constexpr int SMEM_BYTES = 196608 + 1024 + 256;  // stages * stage bytes is 192 KB for both schemes
 constexpr uint32_t TMEM_COLS = 512;
@@ -109,7 +104,7 @@ struct Scheme<2> {
 };
 
 struct Prob {
-  CUtensorMap ta, tb;  // ta: A box {64, 128/CLUSTER, 1} (one piece, one row slice); tb: B box {64, 128, NP}
+  CUtensorMap ta, tb;  // boxes {64, 128, NP}: all pieces of a 128-row, 64-term tile
   float2* out;
   const float* sa;     // operand scales (mixed FP16 scheme) or null
   const float* sb;
@@ -189,25 +184,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int WIN_KB = P.win_kb, LWIN = P.lwin;
   // grouped raster: consecutive CTAs sweep the n-tiles of RASTER_GROUP m-tiles
   const int mt_n = (pr.M + BM - 1) / BM, nt_n = (pr.N + BN - 1) / BN;
-  // Clusters of CLUSTER CTAs share one m-tile (its A tile is multicast) and
-  // take adjacent n-tiles; a CTA whose n-tile is past N computes masked zeros.
-  const int np_n = (nt_n + CLUSTER - 1) / CLUSTER;  // n-tile groups
-  const int crank = static_cast<int>(cluster_ctarank());
-  const int lin = blockIdx.x / CLUSTER;             // cluster index (uniform in the cluster)
-  if (lin >= mt_n * np_n) return;                   // whole cluster outside this problem
-  const int grp = lin / (RASTER_GROUP * np_n);
+  const int lin = blockIdx.x;
+  if (lin >= mt_n * nt_n) return;  // CTA outside this problem
+  const int grp = lin / (RASTER_GROUP * nt_n);
   const int gm0 = grp * RASTER_GROUP;
   const int gsz = min(RASTER_GROUP, mt_n - gm0);
-  const int in_grp = lin - grp * RASTER_GROUP * np_n;
+  const int in_grp = lin - grp * RASTER_GROUP * nt_n;
   const int m0 = (gm0 + in_grp % gsz) * BM;
-  const int n0 = ((in_grp / gsz) * CLUSTER + crank) * BN;
+  const int n0 = (in_grp / gsz) * BN;
   if (pr.tri > 0) {
-    // rows and columns come in blocks of pr.tri (a symmetric product's pair index): a cluster whose
+    // rows and columns come in blocks of pr.tri (a symmetric product's pair index): a tile whose
     // smallest row block lies past its largest column block computes nothing anybody reads
-    const int n_end = min(pr.N, ((in_grp / gsz) * CLUSTER + CLUSTER) * BN);
-    if (m0 / pr.tri > (n_end - 1) / pr.tri) return;  // uniform across the cluster
+    const int n_end = min(pr.N, n0 + BN);
+    if (m0 / pr.tri > (n_end - 1) / pr.tri) return;
   }
-  const uint16_t cmask = static_cast<uint16_t>((1u << CLUSTER) - 1u);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -227,7 +217,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CLUSTER);  // one MMA commit from each CTA of the cluster
+      mbar_init(&empty[s], 1);  // one MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&hfull[b], 1);
@@ -246,7 +236,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // peers' barriers are initialised before any multicast or remote arrive
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -260,12 +249,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         uint8_t* sa = smem + s * STAGE;
-        mbar_expect_tx(&full[s], STAGE);  // own B + every CTA's slice of A
-        // this CTA's row slice of the shared A tile, to every CTA of the cluster
-#pragma unroll
-        for (int pc = 0; pc < NP; ++pc)
-          tma_load_3d_mc(&pr.ta, &full[s], sa + pc * A_PIECE + crank * A_HALF, kb * BK,
-                         m0 + crank * (BM / CLUSTER), pc, cmask);
+        mbar_expect_tx(&full[s], STAGE);  // every piece of the A and B tiles
+        tma_load_3d(&pr.ta, &full[s], sa, kb * BK, m0, 0);
         tma_load_3d(&pr.tb, &full[s], sa + A_STAGE, kb * BK, n0, 0);
       }
     }
@@ -313,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 umma_f16(tmem + COL_L, ad, bd, SC::IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
             }
           }
-          umma_commit_mc(&empty[s], cmask);  // releases the stage in every CTA it was written to
+          umma_commit(&empty[s]);  // releases the stage once its MMAs have read it
         }
         umma_commit(&hfull[hb]);
         if ((w + 1) % LWIN == 0 || w == nwin - 1) umma_commit(lfull);
@@ -397,7 +382,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // no CTA leaves while a peer may still arrive on its barriers
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
@@ -455,7 +439,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     if (op.K % BK || op.K > 2147483647LL || op.M > 2147483647LL || op.N > 2147483647LL) return -1;
     if ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.B)) & 15) return -1;
     if ((op.lda | op.ldb | op.a_piece | op.b_piece) & 7) return -1;
-    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM / CLUSTER, 1, NP, dt)) return -4;
+    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM, NP, NP, dt)) return -4;
     if (!make_map(&P.p[i].tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN, NP, NP, dt)) return -4;
     P.p[i].out = static_cast<float2*>(op.out);
     P.p[i].sa = op.scale_a;
@@ -466,8 +450,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     P.p[i].K = static_cast<int>(op.K);
     P.p[i].mode = op.mode;
     P.p[i].tri = static_cast<int>(op.tri);
-    const int64_t ngrp = ((op.N + BN - 1) / BN + CLUSTER - 1) / CLUSTER;
-    tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ngrp * CLUSTER);
+    tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ((op.N + BN - 1) / BN));
   }
   // the shared-memory opt-in is a per-device function attribute: set it once for every device used
   static std::atomic<uint64_t> attr_set{0};
@@ -489,13 +472,8 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, cc_gemm_split3_tc<NP>, P, ops[0].status, ops[0].timeout_ns);
   if (e == cudaSuccess) e = cudaPeekAtLastError();
   if (e != cudaSuccess) {

@@ -78,7 +78,10 @@ int scratch_for_current_device(double** out) {
   if (!g_na_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess || !p) return CC_ERR_CUDA;
+    if (e != cudaSuccess || !p) {
+      note_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+      return CC_ERR_CUDA;
+    }
     g_na_ptr[dev] = static_cast<double*>(p);
   }
   *out = g_na_ptr[dev];
@@ -116,5 +119,10 @@ extern "C" int cc_ladder_lagrangian_noalloc(const cc_ladder_system* sys, int n_s
     k_noalloc_final<<<1, kNoAllocThreads, 0, st>>>(part, E + i);
     count_launch(2);
   }
-  return cudaPeekAtLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return CC_ERR_CUDA;
+  }
+  return CC_OK;
 }

@@ -136,19 +136,45 @@ class System:
         return int(self.L_vv.shape[0])
 
     def c_struct(self) -> cc_ladder_system:
+        o, v, nj = self.o, self.v, self.nj
+        _shape(self.L_vv, (nj, v, v), "L_vv")
+        _shape(self.t2, (o, o, v, v), "t2")
+        if self.t1 is not None:
+            _shape(self.t1, (o, v), "t1")
+        if self.tbar2 is not None:
+            _shape(self.tbar2, (o, o, v, v), "tbar2")
+        if self.eps is not None:
+            _shape(self.eps, (o + v,), "eps")
+
         def ptr(t):
             if t is None:
                 return None
-            if t.dtype != torch.float64 or not t.is_contiguous():
-                raise ValueError("ladder tensors must be contiguous float64")
-            if not t.is_cuda:
-                raise ValueError("ladder tensors must live on the GPU (the kernels read device memory)")
-            return t.data_ptr()
-        return cc_ladder_system(self.o, self.v, self.nj, ptr(self.L_vv), ptr(self.t1),
+            return _dev_ptr(t, "ladder tensors")
+        return cc_ladder_system(o, v, nj, ptr(self.L_vv), ptr(self.t1),
                                 ptr(self.t2), ptr(self.tbar2), ptr(self.eps))
 
 
+def _shape(t, shape, name):
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _dev_ptr(t, name):
+    """Device address of a contiguous float64 tensor on the current GPU (checks in that order,
+    so that shape and dtype errors are reported without touching CUDA)."""
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float64 tensors")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on the GPU (the kernels read device memory)")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must live on the current CUDA device "
+                         f"(cuda:{torch.cuda.current_device()}), not {t.device}")
+    return t.data_ptr()
+
+
 def _arr(systems: Sequence[System]):
+    if len(systems) < 1:
+        raise ValueError("at least one system")
     arr = (cc_ladder_system * len(systems))()
     for k, s in enumerate(systems):
         arr[k] = s.c_struct()
@@ -156,10 +182,34 @@ def _arr(systems: Sequence[System]):
 
 
 def _ptrs(ts):
-    for t in ts:
-        if t.dtype != torch.float64 or not t.is_contiguous() or not t.is_cuda:
-            raise ValueError("output and amplitude buffers must be contiguous float64 GPU tensors")
-    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    return (ctypes.c_void_p * len(ts))(*[_dev_ptr(t, "output and amplitude buffers") for t in ts])
+
+
+def _outs(ts, systems, like, name):
+    """One buffer per system, each with the shape of that system's `like` tensor (t2 or L_vv)."""
+    ts = list(ts)
+    if len(ts) != len(systems):
+        raise ValueError(f"{name}: one buffer per system ({len(ts)} given for {len(systems)} systems)")
+    for t, s in zip(ts, systems):
+        _shape(t, tuple(getattr(s, like).shape), name)
+    return _ptrs(ts)
+
+
+def _energy(E, n):
+    if E.dim() != 1 or E.numel() < n:
+        raise ValueError(f"E must be a 1-D tensor of at least {n} float64 values")
+    return ctypes.c_void_p(_dev_ptr(E, "E"))
+
+
+def _ws_args(ws):
+    """(device address, size in bytes) of a workspace tensor on the current GPU."""
+    if not ws.is_contiguous():
+        raise ValueError("the workspace must be a contiguous tensor")
+    if not ws.is_cuda:
+        raise ValueError("the workspace must be GPU memory")
+    if ws.device.index != torch.cuda.current_device():
+        raise ValueError(f"the workspace must live on the current CUDA device, not {ws.device}")
+    return ctypes.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size()
 
 
 def _stream(stream):
@@ -193,36 +243,37 @@ def workspace(systems: Sequence[System], prec="mixed", which=CC_WS_STEP, device=
 def _ws(systems, prec, which, ws):
     if ws is None:
         ws = workspace(systems, prec, which)
-    if not ws.is_cuda:
-        raise ValueError("the workspace must be GPU memory")
     return ws
 
 
 def cc_ladder_residual(systems, prec="mixed", ws=None, out=None, stream=None):
     lib = load()
-    ws = _ws(systems, prec, CC_WS_RESIDUAL, ws)
+    arr = _arr(systems)
     out = out or [torch.empty_like(s.t2) for s in systems]
-    _check(lib.cc_ladder_residual(_arr(systems), len(systems), _ptrs(out), _prec(prec),
-                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    po = _outs(out, systems, "t2", "Omega")
+    wp, wn = _ws_args(_ws(systems, prec, CC_WS_RESIDUAL, ws))
+    _check(lib.cc_ladder_residual(arr, len(systems), po, _prec(prec), wp, wn, _stream(stream)))
     return out
 
 
 def cc_ladder_residual_adjoint(systems, prec="mixed", ws=None, out=None, stream=None):
     """dE/dtau_ij^cd = sum_ab tbar_ij^ab g_acbd (the adjoint ladder), one buffer per system."""
     lib = load()
-    ws = _ws(systems, prec, CC_WS_RESIDUAL, ws)
+    arr = _arr(systems)
     out = out or [torch.empty_like(s.t2) for s in systems]
-    _check(lib.cc_ladder_residual_adjoint(_arr(systems), len(systems), _ptrs(out), _prec(prec),
-                                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    po = _outs(out, systems, "t2", "dE/dtau")
+    wp, wn = _ws_args(_ws(systems, prec, CC_WS_RESIDUAL, ws))
+    _check(lib.cc_ladder_residual_adjoint(arr, len(systems), po, _prec(prec), wp, wn, _stream(stream)))
     return out
 
 
 def cc_ladder_density(systems, prec="mixed", ws=None, out=None, stream=None):
     lib = load()
-    ws = _ws(systems, prec, CC_WS_DENSITY, ws)
+    arr = _arr(systems)
     out = out or [torch.empty_like(s.L_vv) for s in systems]
-    _check(lib.cc_ladder_density(_arr(systems), len(systems), _ptrs(out), _prec(prec),
-                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    po = _outs(out, systems, "L_vv", "D")
+    wp, wn = _ws_args(_ws(systems, prec, CC_WS_DENSITY, ws))
+    _check(lib.cc_ladder_density(arr, len(systems), po, _prec(prec), wp, wn, _stream(stream)))
     return out
 
 
@@ -230,69 +281,72 @@ def cc_ladder_density_es(systems, R2, R0, prec="mixed", ws=None, out=None, strea
     """Excited-state density: D with U = R0 * t2 + R2 in place of tau (tbar2 = left doubles L2)."""
     if len(R2) != len(systems) or len(R0) != len(systems):
         raise ValueError("one R2 buffer and one R0 value per system")
-    for s_, r in zip(systems, R2):
-        if tuple(r.shape) != tuple(s_.t2.shape):
-            raise ValueError("R2 must have the shape of t2")
     lib = load()
-    ws = _ws(systems, prec, CC_WS_DENSITY, ws)
+    arr = _arr(systems)
+    pr2 = _outs(R2, systems, "t2", "R2")
     out = out or [torch.empty_like(s.L_vv) for s in systems]
+    po = _outs(out, systems, "L_vv", "D")
     r0 = (ctypes.c_double * len(systems))(*[float(x) for x in R0])
-    for r in R2:
-        _f64(r, "R2")
-    _check(lib.cc_ladder_density_es(_arr(systems), len(systems), _ptrs(R2), r0, _ptrs(out), _prec(prec),
-                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    wp, wn = _ws_args(_ws(systems, prec, CC_WS_DENSITY, ws))
+    _check(lib.cc_ladder_density_es(arr, len(systems), pr2, r0, po, _prec(prec), wp, wn, _stream(stream)))
     return out
 
 
 def cc_ladder_lagrangian(systems, omega=None, prec="mixed", ws=None, E=None, stream=None):
     lib = load()
-    ws = _ws(systems, prec, CC_WS_LAGRANGIAN, ws)
+    arr = _arr(systems)
+    om = _outs(omega, systems, "t2", "Omega") if omega is not None else None
     if E is None:
         E = torch.empty(len(systems), dtype=torch.float64, device=systems[0].L_vv.device)
-    om = _ptrs(omega) if omega is not None else None
-    _check(lib.cc_ladder_lagrangian(_arr(systems), len(systems), ctypes.c_void_p(E.data_ptr()), om,
-                                    _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                                    _stream(stream)))
+    pe = _energy(E, len(systems))
+    wp, wn = _ws_args(_ws(systems, prec, CC_WS_LAGRANGIAN, ws))
+    _check(lib.cc_ladder_lagrangian(arr, len(systems), pe, om, _prec(prec), wp, wn, _stream(stream)))
     return E
 
 
-def cc_ladder_lagrangian_noalloc(systems, omega, E=None, stream=None):
-    """E = sum tbar2 * Omega with no workspace and no device allocation (see the C header)."""
+def cc_ladder_lagrangian_noalloc(systems, omega, E, stream=None):
+    """E = sum tbar2 * Omega with no workspace and no device allocation (see the C header).
+    E is the caller's device buffer of at least len(systems) float64 values: this wrapper
+    allocates nothing either."""
     lib = load()
-    if E is None:
-        E = torch.empty(len(systems), dtype=torch.float64, device=systems[0].L_vv.device)
-    _check(lib.cc_ladder_lagrangian_noalloc(_arr(systems), len(systems), ctypes.c_void_p(E.data_ptr()),
-                                            _ptrs(omega), _stream(stream)))
+    arr = _arr(systems)
+    om = _outs(omega, systems, "t2", "Omega")
+    _check(lib.cc_ladder_lagrangian_noalloc(arr, len(systems), _energy(E, len(systems)), om, _stream(stream)))
     return E
 
 
 def cc_ladder_step(systems, prec="mixed", ws=None, omega=None, D=None, E=None, stream=None):
     lib = load()
-    ws = _ws(systems, prec, CC_WS_STEP, ws)
+    arr = _arr(systems)
     omega = omega or [torch.empty_like(s.t2) for s in systems]
     D = D or [torch.empty_like(s.L_vv) for s in systems]
     if E is None:
         E = torch.empty(len(systems), dtype=torch.float64, device=systems[0].L_vv.device)
-    _check(lib.cc_ladder_step(_arr(systems), len(systems), _ptrs(omega), _ptrs(D),
-                              ctypes.c_void_p(E.data_ptr()), _prec(prec),
-                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    po, pd, pe = _outs(omega, systems, "t2", "Omega"), _outs(D, systems, "L_vv", "D"), _energy(E, len(systems))
+    wp, wn = _ws_args(_ws(systems, prec, CC_WS_STEP, ws))
+    _check(lib.cc_ladder_step(arr, len(systems), po, pd, pe, _prec(prec), wp, wn, _stream(stream)))
     return omega, D, E
 
 
 def cc_ladder_update(systems, omega, out=None, stream=None):
     lib = load()
+    arr = _arr(systems)
+    pom = _outs(omega, systems, "t2", "Omega")
     out = out or [torch.empty_like(s.t2) for s in systems]
-    _check(lib.cc_ladder_update(_arr(systems), len(systems), _ptrs(omega), _ptrs(out), _stream(stream)))
+    po = _outs(out, systems, "t2", "t2_out")
+    _check(lib.cc_ladder_update(arr, len(systems), pom, po, _stream(stream)))
     return out
 
 
 def cc_ladder_status(ws, stream=None) -> int:
-    return int(load().cc_ladder_status(ctypes.c_void_p(ws.data_ptr()), _stream(stream)))
+    return int(load().cc_ladder_status(_ws_args(ws)[0], _stream(stream)))
 
 
 def cc_ladder_debug_wait(flag: torch.Tensor, timeout_ns: int, ws, stream=None):
+    if flag.dtype != torch.int32 or not flag.is_cuda:
+        raise ValueError("the flag must be an int32 GPU tensor")
     _check(load().cc_ladder_debug_wait(ctypes.c_void_p(flag.data_ptr()), int(timeout_ns),
-                                       ctypes.c_void_p(ws.data_ptr()), _stream(stream)))
+                                       _ws_args(ws)[0], _stream(stream)))
 
 
 def cc_ladder_launch_count() -> int:
@@ -315,18 +369,18 @@ def cc_ladder_profile_read():
 
 
 def _f64(t, name):
-    if t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous float64 tensor")
-    if not t.is_cuda:
-        raise ValueError(f"{name} must live on the GPU (the kernels read device memory)")
-    return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(_dev_ptr(t, name))
 
 
 def cc_ladder_t1_transform(L_vv, L_ov, t1, out=None, stream=None):
     """vv block of the T1-transformed Cholesky vectors: L_vv - t1^T L_ov per J."""
     nj, v, _ = L_vv.shape
     o = t1.shape[0]
+    _shape(L_vv, (nj, v, v), "L_vv")
+    _shape(L_ov, (nj, o, v), "L_ov")
+    _shape(t1, (o, v), "t1")
     out = torch.empty_like(L_vv) if out is None else out
+    _shape(out, (nj, v, v), "out")
     _check(load().cc_ladder_t1_transform(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(t1, "t1"),
                                          _f64(out, "out"), _stream(stream)))
     return out
@@ -336,7 +390,10 @@ def cc_ladder_w_backtransform(W_vv, t1, out=None, stream=None):
     """ov block of x^T W y for a vv-only W: -t1 W per J."""
     nj, v, _ = W_vv.shape
     o = t1.shape[0]
+    _shape(W_vv, (nj, v, v), "W_vv")
+    _shape(t1, (o, v), "t1")
     out = torch.empty((nj, o, v), dtype=torch.float64, device=W_vv.device) if out is None else out
+    _shape(out, (nj, o, v), "out")
     _check(load().cc_ladder_w_backtransform(o, v, nj, _f64(W_vv, "W_vv"), _f64(t1, "t1"), _f64(out, "out"),
                                             _stream(stream)))
     return out
@@ -351,8 +408,9 @@ def cc_ladder_mp2_driver(L_ov, prec="mixed", ws=None, out=None, stream=None):
         raise LadderError(-1, "invalid sizes for the driver workspace")
     ws = torch.empty(n, dtype=torch.uint8, device=L_ov.device) if ws is None else ws
     out = torch.empty((o, o, v, v), dtype=torch.float64, device=L_ov.device) if out is None else out
+    _shape(out, (o, o, v, v), "out")
     _check(lib.cc_ladder_mp2_driver(o, v, nj, _f64(L_ov, "L_ov"), _f64(out, "out"), _prec(prec),
-                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+                                    *_ws_args(ws), _stream(stream)))
     return out
 
 
@@ -368,9 +426,12 @@ def cc_ladder_iterate(system, g_drv, n_iter, prec="mixed", ws=None, out=None, dn
             raise LadderError(-1, "invalid system for the iteration workspace")
         ws = torch.empty(n, dtype=torch.uint8, device=system.L_vv.device)
     out = torch.empty_like(system.t2) if out is None else out
+    _shape(out, tuple(system.t2.shape), "out")
     dnorm2 = torch.empty(n_iter, dtype=torch.float64, device=system.L_vv.device) if dnorm2 is None else dnorm2
+    if dnorm2.dim() != 1 or dnorm2.numel() < n_iter:
+        raise ValueError(f"dnorm2 must hold at least n_iter = {n_iter} values")
     _check(lib.cc_ladder_iterate(arr, _f64(g_drv, "g_drv"), int(n_iter), _f64(out, "out"), _f64(dnorm2, "dnorm2"),
-                                 _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+                                 _prec(prec), *_ws_args(ws), _stream(stream)))
     return out, dnorm2
 
 
@@ -378,6 +439,9 @@ def cc_ladder_ov3_gs(L_vv, L_ov, t2, tbar1, R0=1.0, prec="mixed", ws=None, strea
     """Ground-state OV^3 contributions (W_vv [nj, v, v], W_ov [nj, o, v])."""
     lib = load()
     nj, o, v = L_ov.shape
+    _shape(L_vv, (nj, v, v), "L_vv")
+    _shape(t2, (o, o, v, v), "t2")
+    _shape(tbar1, (o, v), "tbar1")
     if ws is None:
         n = int(lib.cc_ladder_ov3_workspace_size(o, v, nj, _prec(prec)))
         if n == 0:
@@ -387,7 +451,7 @@ def cc_ladder_ov3_gs(L_vv, L_ov, t2, tbar1, R0=1.0, prec="mixed", ws=None, strea
     W_ov = torch.empty_like(L_ov)
     _check(lib.cc_ladder_ov3_gs(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(t2, "t2"),
                                 _f64(tbar1, "tbar1"), float(R0), _f64(W_vv, "W_vv"), _f64(W_ov, "W_ov"),
-                                _prec(prec), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+                                _prec(prec), *_ws_args(ws), _stream(stream)))
     return W_vv, W_ov
 
 
@@ -395,6 +459,9 @@ def cc_ladder_ov3_es_abci(L_vv, L_ov, L2, R1, prec="mixed", ws=None, stream=None
     """Excited-state d_abci contributions (W_vv [nj, v, v], W_vo [nj, o, v] = W_ci)."""
     lib = load()
     nj, o, v = L_ov.shape
+    _shape(L_vv, (nj, v, v), "L_vv")
+    _shape(L2, (o, o, v, v), "L2")
+    _shape(R1, (o, v), "R1")
     if ws is None:
         n = int(lib.cc_ladder_ov3_workspace_size(o, v, nj, _prec(prec)))
         if n == 0:
@@ -404,7 +471,7 @@ def cc_ladder_ov3_es_abci(L_vv, L_ov, L2, R1, prec="mixed", ws=None, stream=None
     W_vo = torch.empty_like(L_ov)
     _check(lib.cc_ladder_ov3_es_abci(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(L2, "L2"),
                                      _f64(R1, "R1"), _f64(W_vv, "W_vv"), _f64(W_vo, "W_vo"), _prec(prec),
-                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+                                     *_ws_args(ws), _stream(stream)))
     return W_vv, W_vo
 
 

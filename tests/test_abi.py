@@ -133,3 +133,40 @@ def test_binding_rejects_host_tensors_before_any_call():
         lad._f64(torch.zeros(4, dtype=torch.float64), "x")
     with pytest.raises(ValueError):
         lad.cc_ladder_density_es([s], [], [1.0])
+
+
+def test_binding_checks_lengths_shapes_and_E_on_the_host():
+    # every check below fires before any device pointer is taken, so CPU tensors exercise them
+    import torch
+    f = lambda *sh: torch.zeros(*sh, dtype=torch.float64)
+    s = lad.System(L_vv=f(3, 4, 4), t2=f(2, 2, 4, 4), t1=f(2, 4), tbar2=f(2, 2, 4, 4), eps=f(6))
+    # one output per system, each shaped like the system's t2 (Omega) or L_vv (D)
+    with pytest.raises(ValueError, match="one buffer per system"):
+        lad._outs([f(2, 2, 4, 4), f(2, 2, 4, 4)], [s], "t2", "Omega")
+    with pytest.raises(ValueError, match="one buffer per system"):
+        lad._outs([], [s], "L_vv", "D")
+    with pytest.raises(ValueError, match="shape"):
+        lad._outs([f(2, 2, 4, 5)], [s], "t2", "Omega")
+    with pytest.raises(ValueError, match="shape"):
+        lad._outs([f(3, 4, 5)], [s], "L_vv", "D")
+    # E: 1-D float64 with room for every system
+    with pytest.raises(ValueError, match="at least 2"):
+        lad._energy(f(1), 2)
+    with pytest.raises(ValueError, match="at least 1"):
+        lad._energy(f(1, 1), 1)
+    with pytest.raises(ValueError, match="float64"):
+        lad._energy(torch.zeros(2, dtype=torch.float32), 2)
+    # inconsistent system shapes
+    for bad in (dict(t1=f(2, 5)), dict(tbar2=f(2, 2, 4, 3)), dict(eps=f(5)), dict(L_vv=f(3, 4, 5))):
+        kw = dict(L_vv=s.L_vv, t2=s.t2, t1=s.t1, tbar2=s.tbar2, eps=s.eps)
+        kw.update(bad)
+        with pytest.raises(ValueError, match="shape"):
+            lad.System(**kw).c_struct()
+    with pytest.raises(ValueError, match="at least one system"):
+        lad._arr([])
+    # a host workspace is refused before its address is taken
+    with pytest.raises(ValueError, match="GPU memory"):
+        lad._ws_args(torch.zeros(16, dtype=torch.uint8))
+    # the no-allocation wrapper does not allocate E for the caller
+    with pytest.raises(TypeError):
+        lad.cc_ladder_lagrangian_noalloc([s], [f(2, 2, 4, 4)])
