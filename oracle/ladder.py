@@ -32,7 +32,8 @@ Pins (tests/test_oracle.py): brute force vs rows vs packed, pair
 symmetries, the Euler identity sum L.D = E, central finite differences of E
 (dE/dL = 2D, dE/dtau = transposed ladder), closed forms for nj = 1, one-hot
 L, t1 = 0 and o = 1, homogeneity in L, and a hand-computed example under
-tests/golden/.
+tests/golden/.  ``update_t2`` is pinned by hand values and by one step of
+``oracle.iterate.jacobi`` (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

@@ -10,8 +10,13 @@ Z^K_rs directly, never storing the density:
     W_ab^K = sum_ic d_abic Z^K_ic = R0 L^a_m Y~^K_bm,   Y~^K_bm = t~^cb_im Z^K_ic   (Table I)
     W_ic^K = sum_ab d_abic Z^K_ab = R0 t~^cb_im O^K_bm,  O^K_bm = L^a_m Z^K_ab
 
-with L^K in place of Z^K, as for the V^4 part (D).  ``*_explicit`` forms the
-OV^3 density; ``w_ov3_gs`` is the factorised form.
+with L^K in place of Z^K, as for the V^4 part (D).  ``density_*`` forms the
+OV^3 density; ``w_ov3_*`` is the factorised form.  Pins: the two density
+blocks against hand-computed o = 2, v = 2 values (tests/golden/
+hand_update_es_ov3.json, built so that a swapped occupied or virtual pair
+fails them), the factorised forms against the explicit ones, and central
+finite differences of the OV^3 energy term (tests/test_oracle_ov3.py,
+tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

@@ -70,5 +70,6 @@ def w_backtransform_full(W_full, t1):
 
 def es_amplitudes(t2, r2, r0):
     """U = T2 R0 + R2, the doubles that pair with L2 in the excited-state V^4
-    density (App. A)."""
+    density (App. A).  Pinned through that density by a hand-computed o = 1,
+    v = 2 case with R0 = 2 (tests/golden/hand_update_es_ov3.json)."""
     return float(r0) * np.asarray(t2, dtype=np.float64) + np.asarray(r2, dtype=np.float64)
