@@ -135,10 +135,13 @@ def oracle_sample(h, rows, cols):
     return time.perf_counter() - t0, om, D
 
 
-def sample_spec(v, n_rows=2, n_cols=64):
-    rows = [int(round(k * (v - 1) / max(1, n_rows - 1))) for k in range(n_rows)] if n_rows > 1 else [v // 2]
-    step = max(1, v // n_cols)
-    cols = list(range(0, v, step))[:n_cols]
+def sample_spec(v, block=48, n_cols=8, seed=2202):
+    """One seeded virtual row per pair-block band (rows block*k .. block*k + block - 1) and a seeded
+    spread of n_cols columns: every band of the pair-block sequence is sampled."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    rows = [int(rng.integers(lo, min(lo + block, v))) for lo in range(0, v, block)]
+    cols = sorted(np.random.default_rng(seed + 1).choice(v, size=min(n_cols, v), replace=False).tolist())
     return rows, cols
 
 
