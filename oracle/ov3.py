@@ -23,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["t_tilde", "density_abic_gs", "w_from_abic", "w_ov3_gs", "density_abci_es", "w_from_abci",
-           "w_ov3_es_abci"]
+           "w_ov3_es_abci", "x_ab", "y_ajbi", "v_ajbi", "ytilde_djak", "density_abic_es", "w_ov3_es_abic"]
 
 
 def t_tilde(t2):
@@ -75,3 +75,98 @@ def w_ov3_es_abci(L2, R1, L_vv, L_ov):
     P = np.einsum("jb,Kab->Kaj", R1, L_vv)
     W_vo = np.einsum("jiac,Kaj->Kic", L2, P)
     return W_vv, W_vo
+
+
+# --------------------------------------------------------------------------
+# excited state, the d_abic block (App. A), eight terms
+# --------------------------------------------------------------------------
+# Index layouts: L2[i, j, a, b] = L_ij^ab (left doubles), t2[i, j, a, b] = t_ij^ab,
+# R2 likewise, R1[i, a] = R_i^a, tbar1[m, a] = L^a_m (left singles).  The
+# intermediates of Table I / App. A with C2 = T2:
+
+def x_ab(L2, C2):
+    """X_ab(L2, C2) = L_kl^ad C_kl^bd."""
+    return np.einsum("klad,klbd->ab", L2, C2)
+
+
+def y_ajbi(L2, C2):
+    """Y_ajbi(L2, C2) = L_jl^ad C_il^bd, as [a, j, b, i]."""
+    return np.einsum("jlad,ilbd->ajbi", L2, C2)
+
+
+def v_ajbi(L2, C2):
+    """V_ajbi(L2, C2) = L_kj^ac C_ki^bc, as [a, j, b, i]."""
+    return np.einsum("kjac,kibc->ajbi", L2, C2)
+
+
+def ytilde_djak(L2, t2):
+    """Y~_djak(L2, T2) = L_mj^ed t~_mk^ea, as [d, j, a, k]."""
+    return np.einsum("mjed,mkea->djak", L2, t_tilde(t2))
+
+
+def density_abic_es(tbar1, L2, t2, R0, R1, R2):
+    """d^es_abic of App. A as printed, [a, b, i, c]:
+
+        L^a_m t~^cb_im R0 + L^a_m (2 R~^bc_mi - R~^cb_mi) + 2 X_ab R^c_i
+        - (V_akbi + Y_akbi) R^c_k + L^ad_mk t~^bc_mi R^d_k - L^ad_mn t^bc_mn R^d_i
+        + Y~_akci R^b_k - X_ac R^b_i
+
+    with X, Y, V, Y~ of (L2, T2) and R~ built from R2 as t~ from T2 (Table I's
+    caption: C~_ij^ab = 2 C_ij^ab - C_ji^ab)."""
+    tbar1 = np.asarray(tbar1, dtype=np.float64)
+    L2 = np.asarray(L2, dtype=np.float64)
+    t2 = np.asarray(t2, dtype=np.float64)
+    R1 = np.asarray(R1, dtype=np.float64)
+    tt, Rt = t_tilde(t2), t_tilde(R2)
+    X = x_ab(L2, t2)
+    VY = v_ajbi(L2, t2) + y_ajbi(L2, t2)                     # [a, k, b, i]
+    Yt = ytilde_djak(L2, t2)                                 # [a, k, c, i] read as Y~_akci
+    d = R0 * np.einsum("ma,imcb->abic", tbar1, tt)                                   # L^a_m t~^cb_im R0
+    d += np.einsum("ma,mibc->abic", tbar1, 2.0 * Rt) - np.einsum("ma,micb->abic", tbar1, Rt)
+    d += 2.0 * np.einsum("ab,ic->abic", X, R1)                                       # 2 X_ab R^c_i
+    d -= np.einsum("akbi,kc->abic", VY, R1)                                          # -(V + Y)_akbi R^c_k
+    d += np.einsum("mkad,mibc,kd->abic", L2, tt, R1)                                 # L^ad_mk t~^bc_mi R^d_k
+    d -= np.einsum("mnad,mnbc,id->abic", L2, t2, R1)                                 # -L^ad_mn t^bc_mn R^d_i
+    d += np.einsum("akci,kb->abic", Yt, R1)                                          # Y~_akci R^b_k
+    d -= np.einsum("ac,ib->abic", X, R1)                                             # -X_ac R^b_i
+    return d
+
+
+def w_ov3_es_abic(tbar1, L2, t2, R0, R1, R2, L_vv, L_ov):
+    """(W_vv[K, a, b], W_ov[K, i, c]) = (sum_ic d_abic L^K_ic, sum_ab d_abic L^K_ab) for d^es_abic,
+    term by term through three-index intermediates, never the OV^3 array (Sec. II.C), with L^K in
+    place of Z^K.  The pair matrix of the first two terms is P^cb_im = R0 t~^cb_im + 2 R~^bc_mi -
+    R~^cb_mi; the others go through X, V + Y, Y~, W_am = L^ad_mk R^d_k and B_iamn = L^ad_mn R^d_i."""
+    tbar1 = np.asarray(tbar1, dtype=np.float64)
+    L2 = np.asarray(L2, dtype=np.float64)
+    t2 = np.asarray(t2, dtype=np.float64)
+    R1 = np.asarray(R1, dtype=np.float64)
+    tt, Rt = t_tilde(t2), t_tilde(R2)
+    P = R0 * tt + 2.0 * Rt.transpose(1, 0, 3, 2) - Rt.transpose(1, 0, 2, 3)   # P[i, m, c, b] = P^cb_im
+    X = x_ab(L2, t2)
+    VY = v_ajbi(L2, t2) + y_ajbi(L2, t2)
+    Yt = ytilde_djak(L2, t2)
+    Wam = np.einsum("mkad,kd->am", L2, R1)
+    B = np.einsum("mnad,id->iamn", L2, R1)
+    # terms 1-2: L^a_m P^cb_im
+    W_vv = np.einsum("ma,Kbm->Kab", tbar1, np.einsum("imcb,Kic->Kbm", P, L_ov))
+    W_ov = np.einsum("imcb,Kbm->Kic", P, np.einsum("ma,Kab->Kbm", tbar1, L_vv))
+    # term 3: 2 X_ab R^c_i
+    W_vv += 2.0 * np.einsum("ab,K->Kab", X, np.einsum("ic,Kic->K", R1, L_ov))
+    W_ov += 2.0 * np.einsum("ic,K->Kic", R1, np.einsum("ab,Kab->K", X, L_vv))
+    # term 4: -(V + Y)_akbi R^c_k
+    W_vv -= np.einsum("akbi,Kik->Kab", VY, np.einsum("kc,Kic->Kik", R1, L_ov))
+    W_ov -= np.einsum("kc,Kik->Kic", R1, np.einsum("akbi,Kab->Kik", VY, L_vv))
+    # term 5: W_am t~^bc_mi
+    W_vv += np.einsum("am,Kbm->Kab", Wam, np.einsum("mibc,Kic->Kbm", tt, L_ov))
+    W_ov += np.einsum("mibc,Kbm->Kic", tt, np.einsum("am,Kab->Kbm", Wam, L_vv))
+    # term 6: -B_iamn t^bc_mn
+    W_vv -= np.einsum("iamn,Kbimn->Kab", B, np.einsum("mnbc,Kic->Kbimn", t2, L_ov))
+    W_ov -= np.einsum("iamn,mnbc,Kab->Kic", B, t2, L_vv)
+    # term 7: Y~_akci R^b_k
+    W_vv += np.einsum("kb,Kak->Kab", R1, np.einsum("akci,Kic->Kak", Yt, L_ov))
+    W_ov += np.einsum("akci,Kak->Kic", Yt, np.einsum("kb,Kab->Kak", R1, L_vv))
+    # term 8: -X_ac R^b_i
+    W_vv -= np.einsum("ib,Kai->Kab", R1, np.einsum("ac,Kic->Kai", X, L_ov))
+    W_ov -= np.einsum("ac,Kai->Kic", X, np.einsum("ib,Kab->Kai", R1, L_vv))
+    return W_vv, W_ov

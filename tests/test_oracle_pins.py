@@ -143,3 +143,96 @@ def test_planted_ov3_transpositions_fail_the_golden_values():
     }
     for name, bad in wrong_es.items():
         assert not np.allclose(bad, A(e["d"])), name
+
+
+# ------------------------------------------------------------------ excited-state d_abic (App. A)
+def _dense(entries, shape):
+    x = np.zeros(shape)
+    for e in entries:
+        x[tuple(e[:-1])] = e[-1]
+    return x
+
+
+def test_density_abic_es_hand_values():
+    c = G["ov3_es_abic_Rtilde"]
+    z2 = np.zeros((2, 2, 2, 2))
+    d = V.density_abic_es(A(c["tbar1"]), z2, z2, 0.0, np.zeros((2, 2)), A(c["R2"]))
+    assert np.allclose(d, A(c["d"]), rtol=0, atol=1e-14)
+    c = G["ov3_es_abic_R1_sparse"]
+    L2 = _dense(c["L2_nonzero"], (2, 2, 2, 2))
+    t2 = _dense(c["t2_nonzero"], (2, 2, 2, 2))
+    R1 = _dense(c["R1_nonzero"], (2, 2))
+    assert np.array_equal(L2, L2.transpose(1, 0, 3, 2)) and np.array_equal(t2, t2.transpose(1, 0, 3, 2))
+    d = V.density_abic_es(np.zeros((2, 2)), L2, t2, 0.0, R1, np.zeros((2, 2, 2, 2)))
+    assert np.allclose(d, _dense(c["d_nonzero"], (2, 2, 2, 2)), rtol=0, atol=1e-14)
+
+
+def _es_case(o, v, seed):
+    s, tb1, L2 = synth.make_pair(o, v, 5, 4.0, seed=seed)
+    rng = np.random.default_rng(seed)
+    R1 = rng.standard_normal((o, v))
+    R2 = rng.standard_normal((o, o, v, v))
+    R2 = 0.5 * (R2 + R2.transpose(1, 0, 3, 2))
+    return s, tb1, L2, R1, R2
+
+
+def test_density_abic_es_reduces_to_the_ground_state_and_cancels_in_one_orbital_spaces():
+    s, tb1, L2, R1, R2 = _es_case(3, 6, 21)
+    # no excitation: the ground-state block (itself pinned by hand values)
+    assert np.allclose(V.density_abic_es(tb1, L2, s.t2, 0.8, 0 * R1, 0 * R2), V.density_abic_gs(tb1, s.t2, 0.8),
+                       rtol=0, atol=1e-15)
+    # one occupied or one virtual orbital (pair-symmetric inputs): the six R1 terms cancel exactly,
+    # 2 X - X - X and -2 (V + Y) + (L t~ R) + Y~ pair off term by term
+    for o, v in ((1, 6), (5, 1)):
+        s1, tb, L2b, R1b, _ = _es_case(o, v, 5)
+        d = V.density_abic_es(np.zeros_like(tb), L2b, s1.t2, 0.0, R1b, np.zeros_like(s1.t2))
+        assert np.max(np.abs(d)) < 1e-13 * max(1.0, np.max(np.abs(L2b)) * np.max(np.abs(s1.t2)))
+
+
+def test_w_ov3_es_abic_factorised_and_finite_differences():
+    s, tb1, L2, R1, R2 = _es_case(3, 7, 9)
+    d = V.density_abic_es(tb1, L2, s.t2, 0.6, R1, R2)
+    We, Wo = V.w_from_abic(d, s.L_vv, s.L_ov)
+    Fe, Fo = V.w_ov3_es_abic(tb1, L2, s.t2, 0.6, R1, R2, s.L_vv, s.L_ov)
+    assert np.linalg.norm(Fe - We) < 1e-13 * np.linalg.norm(We)
+    assert np.linalg.norm(Fo - Wo) < 1e-13 * np.linalg.norm(Wo)
+
+    def energy(Lvv, Lov):       # sum_abic d_abic (ab|ic), (ab|ic) = sum_K L^K_ab L^K_ic
+        return float(np.einsum("abic,Kab,Kic->", d, Lvv, Lov))
+
+    h = 1e-6
+    for (K, a, b) in [(0, 1, 2), (4, 6, 0)]:
+        Lp = s.L_vv.copy(); Lp[K, a, b] += h
+        Lm = s.L_vv.copy(); Lm[K, a, b] -= h
+        fd = (energy(Lp, s.L_ov) - energy(Lm, s.L_ov)) / (2 * h)
+        assert abs(fd - Fe[K, a, b]) < 1e-7 * max(1.0, abs(fd))
+    for (K, i, c) in [(1, 0, 3), (3, 2, 6)]:
+        Lp = s.L_ov.copy(); Lp[K, i, c] += h
+        Lm = s.L_ov.copy(); Lm[K, i, c] -= h
+        fd = (energy(s.L_vv, Lp) - energy(s.L_vv, Lm)) / (2 * h)
+        assert abs(fd - Fo[K, i, c]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_planted_es_abic_mistakes_fail_the_pins():
+    c = G["ov3_es_abic_R1_sparse"]
+    L2 = _dense(c["L2_nonzero"], (2, 2, 2, 2))
+    t2 = _dense(c["t2_nonzero"], (2, 2, 2, 2))
+    R1 = _dense(c["R1_nonzero"], (2, 2))
+    ref = _dense(c["d_nonzero"], (2, 2, 2, 2))
+    good = V.density_abic_es(np.zeros((2, 2)), L2, t2, 0.0, R1, np.zeros((2, 2, 2, 2)))
+    tt = V.t_tilde(t2)
+    wrong = {
+        "t~ virtual pair swapped in the W_am term": good - np.einsum("mkad,mibc,kd->abic", L2, tt, R1)
+        + np.einsum("mkad,micb,kd->abic", L2, tt, R1),
+        "sign of the B t term": good + 2 * np.einsum("mnad,mnbc,id->abic", L2, t2, R1),
+        "2 Y in place of Y~ (the Sec. II.C variant)": good - np.einsum("akci,kb->abic", V.ytilde_djak(L2, t2), R1)
+        + 2 * np.einsum("akci,kb->abic", V.y_ajbi(L2, t2), R1),
+        "X_ab R^c_i without its 2": good - np.einsum("ab,ic->abic", V.x_ab(L2, t2), R1),
+    }
+    for name, bad in wrong.items():
+        assert not np.allclose(bad, ref), name
+    c = G["ov3_es_abic_Rtilde"]
+    z2 = np.zeros((2, 2, 2, 2))
+    Rt = V.t_tilde(A(c["R2"]))
+    plain = np.einsum("ma,imcb->abic", A(c["tbar1"]), Rt)   # the U-tilde reading, L^a_m R~^cb_im
+    assert not np.allclose(plain, A(c["d"]))
