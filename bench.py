@@ -9,9 +9,12 @@ the packed (+-) algorithm's flop formula
     F = 2 P+ v^2 N_J + 4 (P+^2 Q+ + P-^2 Q-) + 2 v^4 N_J,
     P+- = v(v+-1)/2, Q+- = o(o+-1)/2.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--split]
 Under torchrun each rank runs its own system (weak scaling, no collective on
-the data path); value = N * F / (max over ranks of the step time).
+the data path); value = N * F / (max over ranks of the step time).  With
+--split the ranks share one system: each runs its LPT share of the pair
+blocks (cc_ladder_step_blocks), the partial D meet in one NCCL
+reduce-scatter and E in one all-reduce; value = F / (max step time).
 """
 from __future__ import annotations
 
@@ -66,6 +69,26 @@ def peaks():
         except Exception:
             pass
     return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
+
+
+def dgemm_peak(torch, n=8192, reps=5):
+    """FP64 tensor-core peak of this GPU, measured here: cuBLAS DGEMM n^3 (torch.matmul, float64),
+    best of `reps` after one warm-up, CUDA events.  TFLOP/s."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 class Clocks:
@@ -250,7 +273,9 @@ def run_ours(args):
     lad.load()
     o, v, nj, lam = WORKLOADS[args.workload]
     F = counted_flops(o, v, nj)
-    d = synth.make_pair_torch(o, v, nj, lam, seed=2202 + 17 * rank, device="cuda")
+    split = args.split and world > 1
+    # weak scaling: every rank its own system; --split: one system, its pair blocks dealt over the ranks
+    d = synth.make_pair_torch(o, v, nj, lam, seed=2202 + (0 if args.split else 17 * rank), device="cuda")
     sd = lad.System(L_vv=d["L_vv"], t2=d["t2"], t1=d["t1"], tbar2=d["tbar2"], eps=d["eps"])
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -259,9 +284,16 @@ def run_ours(args):
     D = [torch.empty_like(sd.L_vv)]
     E = torch.empty(1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    mine = shard.rank_blocks(sd, rank, world) if split else None
 
     def step():
-        lad.cc_ladder_step([sd], prec=args.prec, ws=ws, omega=om, D=D, E=E, stream=stream)
+        if not split:
+            lad.cc_ladder_step([sd], prec=args.prec, ws=ws, omega=om, D=D, E=E, stream=stream)
+            return
+        # this rank's pair blocks, then D summed by one reduce-scatter and E by one all-reduce
+        lad.cc_ladder_step_blocks(sd, mine, prec=args.prec, ws=ws, omega=om[0], D=D[0], E=E, stream=stream)
+        shard.reduce_scatter_D(D[0], world)
+        dist.all_reduce(E, op=dist.ReduceOp.SUM)
 
     for _ in range(args.warmup):
         step()
@@ -287,14 +319,16 @@ def run_ours(args):
     lad.cc_ladder_profile(False)
     status = lad.cc_ladder_status(ws)
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max, value = shard.aggregate_step_time(ms, world, F)
+    # weak: world systems of F each; split: one system of F over all ranks
+    ms_max, value = shard.aggregate_step_time(ms, world, F / world if split else F)
 
     pk = peaks()
     gemm_ms_step = gemm_ms / args.steps
     achieved = F / (gemm_ms_step * 1e-3) / 1e12
     nprod = PREC[args.prec][0]
     if args.prec == "fp64":
-        peak_useful, basis = 1.25, "nominal FP64 tensor rate (not measured)"
+        peak_useful = dgemm_peak(torch)
+        basis = "cuBLAS DGEMM 8192^3 measured in this run (torch.matmul float64, best of 5)"
     else:
         # FP16 and BF16 share the dense tensor rate: the measured BF16 figure serves both
         peak_useful = pk["bf16_sustained"] / nprod
@@ -387,11 +421,13 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "strong" if split else "weak",
             "vs_baseline": None, "dtype": PREC[args.prec][1],
             "data": "synthetic (seeded device generator: MP2 amplitudes from random symmetric Cholesky vectors)",
             "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "global_batch": world,
-                       "parallelism": f"independent systems, one per GPU ({world})",
+                       "parallelism": (f"one system, pair blocks dealt over {world} GPUs (LPT), D by reduce-scatter"
+                                       if split else f"independent systems, one per GPU ({world})"),
                        "l2": "inputs larger than L2 (55 GB resident), no flush needed",
                        "counted_flops_per_system": F},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -423,7 +459,7 @@ def run_batch(args):
     torch.cuda.empty_cache()
     F = sum(counted_flops(o, v, nj) for o, v, nj in sizes)
     tuned = autotune.tune(systems, prec=args.prec, reps=1) if args.autotune else {"block": 0, "win": 0, "source": "default"}
-    ws = lad.workspace(systems, args.prec)
+    ws = lad.workspace(systems, args.prec, batched=True)
     om = [torch.empty_like(s.t2) for s in systems]
     D = [torch.empty_like(s.L_vv) for s in systems]
     E = torch.empty(len(systems), dtype=torch.float64, device="cuda")
@@ -471,6 +507,122 @@ def run_batch(args):
     return 0
 
 
+def run_autograd(args):
+    """Forward + backward of the differentiable ladder energy E(L, tau, tbar) at one workload
+    (default the gradient case o=30, v=250, N_J=1200) in the mixed path.  Counted flops: the
+    forward is the residual route (g-build + ladder) and the E reduction; the backward is dE/dL
+    (Gamma + D), dE/dtau (adjoint ladder: g-build + ladder) and dE/dtbar (g-build + ladder)."""
+    import torch
+    from paper_2202_02019_gb300 import autograd as AG
+    from paper_2202_02019_gb300 import ladder as lad
+    from paper_2202_02019_gb300 import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lad.load()
+    o, v, nj, lam = WORKLOADS[args.workload]
+    d = synth.make_pair_torch(o, v, nj, lam, seed=2202, device="cuda")
+    tau = (d["t2"] + torch.einsum("ic,jd->ijcd", d["t1"], d["t1"])).contiguous()
+    L = d["L_vv"].clone().requires_grad_(True)
+    T = tau.clone().requires_grad_(True)
+    B = d["tbar2"].clone().requires_grad_(True)
+    pvp, pvm = v * (v + 1) // 2, v * (v - 1) // 2
+    qop, qom = o * (o + 1) // 2, o * (o - 1) // 2
+    f_res = 2.0 * pvp * v * v * nj + 4.0 * (pvp * pvp * qop + pvm * pvm * qom) / 2
+    f_den = 4.0 * (pvp * pvp * qop + pvm * pvm * qom) / 2 + 2.0 * float(v) ** 4 * nj
+    F = f_res + (f_den + 2 * f_res)
+
+    def step():
+        L.grad = T.grad = B.grad = None
+        E = AG.ladder_energy(L, T, B, prec=args.prec)
+        E.backward()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = lad.cc_ladder_launch_count()
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "differentiable ladder energy: forward + backward useful TFLOP/s", "value": F / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": PREC[args.prec][1],
+            "data": "synthetic (seeded device generator)",
+            "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}",
+                       "counted_flops": {"forward": f_res, "backward": f_den + 2 * f_res}},
+            "gpu_launches": (lad.cc_ladder_launch_count() - n0), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fp64cmp(args):
+    """The plain FP64 path at one workload: its useful TFLOP/s against the FP64 DGEMM peak
+    measured here, and the split paths' errors against it over the full Omega, D and E."""
+    import torch
+    from paper_2202_02019_gb300 import ladder as lad
+    from paper_2202_02019_gb300 import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lad.load()
+    o, v, nj, lam = WORKLOADS[args.workload]
+    F = counted_flops(o, v, nj)
+    d = synth.make_pair_torch(o, v, nj, lam, seed=2202, device="cuda")
+    sd = lad.System(L_vv=d["L_vv"], t2=d["t2"], t1=d["t1"], tbar2=d["tbar2"], eps=d["eps"])
+    peak = dgemm_peak(torch)
+    res = {}
+
+    def timed_step(prec, warm=True):
+        ws = lad.workspace([sd], prec)
+        om = [torch.empty_like(sd.t2)]
+        D = [torch.empty_like(sd.L_vv)]
+        E = torch.empty(1, dtype=torch.float64, device="cuda")
+        if warm:
+            lad.cc_ladder_step([sd], prec=prec, ws=ws, omega=om, D=D, E=E)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lad.cc_ladder_step([sd], prec=prec, ws=ws, omega=om, D=D, E=E)
+        e1.record()
+        torch.cuda.synchronize()
+        st = lad.cc_ladder_status(ws)
+        del ws
+        torch.cuda.empty_cache()
+        return om[0], D[0], float(E[0]), e0.elapsed_time(e1), st
+
+    def frob(a, b):
+        # chunked over the leading index: no full-size temporary at the retinal size
+        num = den = 0.0
+        for k in range(a.shape[0]):
+            num += float(torch.sum((a[k] - b[k]) ** 2))
+            den += float(torch.sum(b[k] ** 2))
+        return (num / den) ** 0.5
+
+    # at the retinal size one FP64 step is about an hour of FP64 tensor work: time it cold, once
+    with Clocks(0) as clk:
+        om64, D64, E64, ms64, st64 = timed_step("fp64", warm=args.workload != "retinal")
+    res["fp64"] = {"ms": ms64, "tflops": F / (ms64 * 1e-3) / 1e12, "status": st64}
+    for prec in ("mixed", "fp16x2"):
+        om, D, E, ms, st = timed_step(prec)
+        res[prec] = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12, "status": st, "speedup_over_fp64": ms64 / ms,
+                     "rel_err_omega_vs_fp64": frob(om, om64), "rel_err_D_vs_fp64": frob(D, D64),
+                     "rel_err_E_vs_fp64": abs(E - E64) / abs(E64)}
+        del om, D
+    line = {"metric": "plain FP64 path useful TFLOP/s; split paths' errors against it (full tensors)",
+            "value": res["fp64"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": PREC["fp64"][1], "data": "synthetic (seeded device generator)",
+            "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "counted_flops": F,
+                       "fp64_warmup_steps": 0 if args.workload == "retinal" else 1},
+            "roofline": {"bound": "tensor", "achieved": res["fp64"]["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": res["fp64"]["tflops"] / peak, "traffic": None, "kernel": "cc_gemm_f64_dmma (step)",
+                         "peak_basis": "cuBLAS DGEMM 8192^3 measured in this run (torch.matmul float64, best of 5)"},
+            "paths": res, "E_fp64": E64, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,6 +635,12 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="batch24: pick tuning knobs with the autotuner")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, oracle sample and small-config legs")
     ap.add_argument("--no-small", action="store_true", help="skip the small-config FP64-vs-mixed leg")
+    ap.add_argument("--mode", default="step", choices=["step", "autograd", "fp64cmp"],
+                    help="step: the timed ladder step (default); autograd: forward + backward of E(L, tau, tbar); "
+                         "fp64cmp: the FP64 path against the measured DGEMM peak, split paths' errors against it")
+    ap.add_argument("--split", action="store_true",
+                    help="under torchrun: one system sharded over the ranks by pair blocks (strong scaling) "
+                         "instead of one system per rank (weak scaling)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -490,6 +648,10 @@ def main():
         return run_reference(args)
     if args.workload == "batch24":
         return run_batch(args)
+    if args.mode == "autograd":
+        return run_autograd(args)
+    if args.mode == "fp64cmp":
+        return run_fp64cmp(args)
     return run_ours(args)
 
 

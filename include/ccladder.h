@@ -35,8 +35,16 @@
  *     device-side errors (bounded waits that gave up) are latched in the
  *     workspace and reported by cc_ladder_status().  Each call clears the
  *     latched status at its start, so read it after the call it concerns.
- *   - n_sys > 1 runs independent systems back to back on `stream`, sharing
- *     one workspace sized by cc_ladder_workspace_size() over the whole list.
+ *   - n_sys > 1 runs independent systems on `stream`.  With a workspace of
+ *     cc_ladder_workspace_size(sys, n_sys, p, which) bytes they run back to
+ *     back, sharing it.  With at least cc_ladder_workspace_size(sys, n_sys, p,
+ *     which | CC_WS_BATCH) bytes (each system's prepared operands plus
+ *     scratch for up to 8 pair blocks in flight) the batched schedule runs
+ *     instead: every contraction launch carries pair blocks of up to 8
+ *     systems, the ones with the most work left, pulled tile by tile from a
+ *     device queue.  Both give the same bits for the split precisions: every
+ *     output tile is computed the same way, and each system's pair blocks
+ *     keep their order.
  *   - Return codes: 0 or a negative CC_ERR_* value; no host aborts, no
  *     exceptions across the ABI.
  */
@@ -71,12 +79,14 @@ enum {
   CC_ERR_SIZE = -6        /* request larger than a fixed-size device scratch   */
 };
 
-/* which-flags for cc_ladder_workspace_size */
+/* which-flags for cc_ladder_workspace_size.  CC_WS_BATCH, or-ed with the
+ * others, asks for the size of the batched schedule (see n_sys above). */
 enum {
   CC_WS_RESIDUAL = 1,
   CC_WS_DENSITY = 2,
   CC_WS_LAGRANGIAN = 4,
-  CC_WS_STEP = 7
+  CC_WS_STEP = 7,
+  CC_WS_BATCH = 8
 };
 
 typedef struct {
@@ -145,6 +155,31 @@ int cc_ladder_step(const cc_ladder_system* sys, int n_sys,
                    double* const* omega, double* const* D, double* E,
                    cc_precision p, void* ws, size_t ws_bytes, void* stream);
 
+/* Sharding a system over several GPUs (pair blocks, the virtual-pair
+ * blocking of Sec. II.B's restricted loops a <= b: block (alpha <= beta)
+ * holds the pairs a <= b with a in virtual-row block alpha and b in block
+ * beta, blocks of `edge` rows, numbered alpha-major, beta = alpha .. last).
+ * cc_ladder_pair_blocks returns their number and the edge for this system
+ * under the current tuning (host only, no device work).
+ * cc_ladder_step_blocks runs cc_ladder_step restricted to the n_blocks
+ * distinct pair blocks listed in the HOST array `blocks`:
+ *   omega   [o][o][v][v]  Omega_ij^ab and Omega_ij^ba for the pairs a <= b of
+ *                         those blocks (other elements are not touched);
+ *   D_part  [nj][v][v]    the contribution of those blocks to D (overwritten);
+ *   E_part  [1]           sum over those blocks' pairs of tbar . Omega.
+ * Over a partition of the blocks the omegas are disjoint and complete, and
+ * the D_part and E_part sum to D and E (up to the order of the additions: a
+ * multi-GPU run finishes D with one reduce-scatter and E with one all-reduce).
+ * The outputs of a pair block do not depend on the other blocks of the list:
+ * on the split precisions a shard's omega entries are the same bits as those
+ * of cc_ladder_step (the FP64 path adds split-K chunks with atomics, so there
+ * they agree up to the order of those additions).
+ * Workspace: CC_WS_STEP for this one system; n_sys is 1. */
+int cc_ladder_pair_blocks(const cc_ladder_system* sys, int32_t* count, int32_t* edge);
+int cc_ladder_step_blocks(const cc_ladder_system* sys, const int32_t* blocks, int n_blocks,
+                          double* omega, double* D_part, double* E_part, cc_precision p,
+                          void* ws, size_t ws_bytes, void* stream);
+
 /* Jacobi amplitude step t'_ij^ab = t_ij^ab + Omega_ij^ab /
  * (eps_i + eps_j - eps_a - eps_b), in FP64 (the paper leaves the solver
  * step unstated; this is the orbital-energy-denominator update).
@@ -206,6 +241,27 @@ int cc_ladder_ov3_es_abci(int32_t o, int32_t v, int32_t nj, const double* L_vv, 
                           const double* L2, const double* R1, double* W_vv, double* W_vo,
                           cc_precision p, void* ws, size_t ws_bytes, void* stream);
 
+/* Excited-state d_abic block (App. A, eight terms, taken as printed):
+ *   d^es_abic = L^a_m t~^cb_im R0 + L^a_m (2 R~^bc_mi - R~^cb_mi) + 2 X_ab R^c_i
+ *             - (V_akbi + Y_akbi) R^c_k + L^ad_mk t~^bc_mi R^d_k - L^ad_mn t^bc_mn R^d_i
+ *             + Y~_akci R^b_k - X_ac R^b_i
+ * with X_ab = L^ad_kl t^bd_kl, Y_ajbi = L^ad_jl t^bd_il, V_ajbi = L^ac_kj t^bc_ki,
+ * Y~_djak = L^ed_mj t~^ea_mk (Table I, App. A), t~ = 2 t_ij - t_ji and R~ likewise,
+ * and its contributions to the three-index intermediates (Sec. II.C), L^K in
+ * place of Z^K, never forming the OV^3 array:
+ *     W_vv[K][a][b] = sum_ic d_abic L^K_ic,   W_ov[K][i][c] = sum_ab d_abic L^K_ab.
+ * tbar1 [o][v] = L^a_m (left singles), L2 [o][o][v][v] (left doubles) and
+ * t2, R2 [o][o][v][v] pair symmetric, R1 [o][v] = R_i^a; outputs overwritten.
+ * The large contractions run on the FP64 DMMA engine for CC_PREC_FP64 and on
+ * split BF16 for either split precision, the thin ones in FP64.  Workspace:
+ * cc_ladder_ov3_es_abic_workspace_size() bytes, 256-byte aligned (it holds
+ * the O^2V^2 intermediates V + Y and Y~, (o v)^2 doubles each). */
+size_t cc_ladder_ov3_es_abic_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p);
+int cc_ladder_ov3_es_abic(int32_t o, int32_t v, int32_t nj, const double* L_vv, const double* L_ov,
+                          const double* tbar1, const double* L2, const double* t2, double R0,
+                          const double* R1, const double* R2, double* W_vv, double* W_ov,
+                          cc_precision p, void* ws, size_t ws_bytes, void* stream);
+
 /* MP2-like driver of the doubles equations from the occupied-virtual block
  * of the Cholesky vectors (Sec. II.A):
  *     g[i][j][a][b] = g_aibj = sum_J L^J_ia L^J_jb      (t2 layout, [o][o][v][v])
@@ -235,6 +291,12 @@ size_t cc_ladder_iterate_workspace_size(const cc_ladder_system* sys, cc_precisio
 int cc_ladder_iterate(const cc_ladder_system* sys, const double* g_drv, int n_iter,
                       double* t2_out, double* dnorm2, cc_precision p,
                       void* ws, size_t ws_bytes, void* stream);
+
+/* x[k] *= factor * g[0] for k < n, on the device (g: a device double, or NULL
+ * for 1).  The chain rule of the differentiable energy: dE/dL = 2 D times the
+ * incoming gradient of E (Eq. integral_contraction carries the 2), dE/dtau
+ * and dE/dtbar times that gradient, without a host round trip. */
+int cc_ladder_scale_by(double* x, int64_t n, double factor, const double* g, void* stream);
 
 /* Synchronises `stream`, then returns and clears the device-side status
  * latched in `ws` by earlier calls (CC_OK or CC_ERR_TIMEOUT), or

@@ -13,7 +13,9 @@ Gamma tiles instead of storing them (the storage policy of App. A):
 dE/dL = 2D holds for pair-symmetric tau and tbar (tau_ij^cd = tau_ji^dc), the
 precondition of the library's packed algorithm; a perturbation direction
 that breaks the pair symmetry of tau or tbar is outside that domain.
-Nothing V^4-sized is saved for backward: only the three inputs.
+Nothing V^4-sized is saved for backward: only the three inputs.  The
+chain-rule factors (2 and the incoming gradient of E) are applied by the
+library (cc_ladder_scale_by), so this module does no arithmetic itself.
 """
 from __future__ import annotations
 
@@ -36,12 +38,13 @@ class LadderEnergy(torch.autograd.Function):
         L_vv, tau, tbar2 = ctx.saved_tensors
         sysd = lad.System(L_vv=L_vv, t2=tau, tbar2=tbar2)
         dL = dtau = dtbar = None
+        g = gE.detach().to(device=L_vv.device, dtype=torch.float64).contiguous()
         if ctx.needs_input_grad[0]:
-            dL = lad.cc_ladder_density([sysd], prec=ctx.prec)[0].mul_(2.0 * gE)
+            dL = lad.cc_ladder_scale_by(lad.cc_ladder_density([sysd], prec=ctx.prec)[0], 2.0, g)
         if ctx.needs_input_grad[1]:
-            dtau = lad.cc_ladder_residual_adjoint([sysd], prec=ctx.prec)[0].mul_(gE)
+            dtau = lad.cc_ladder_scale_by(lad.cc_ladder_residual_adjoint([sysd], prec=ctx.prec)[0], 1.0, g)
         if ctx.needs_input_grad[2]:
-            dtbar = lad.cc_ladder_residual([sysd], prec=ctx.prec)[0].mul_(gE)
+            dtbar = lad.cc_ladder_scale_by(lad.cc_ladder_residual([sysd], prec=ctx.prec)[0], 1.0, g)
         return dL, dtau, dtbar, None
 
 

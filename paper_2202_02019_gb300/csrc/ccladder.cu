@@ -463,11 +463,13 @@ __global__ void k_jacobi(const double* __restrict__ g, const double* __restrict_
 }
 
 // Doubles as an (o v) x (o v) matrix for the OV^3 contributions:
-// P[(i,c)][(m,b)] = alpha x_im^cb + beta x_mi^cb (zero for columns past o v), split into
-// the operand format; (alpha, beta) = (2, -1) gives t~ = 2 t - t^T, (1, 0) the amplitudes
+// P[(i,c)][(m,b)] = alpha x_im^cb + beta x_mi^cb (+ gamma u_im^cb + delta u_mi^cb with a second
+// array u) (zero for columns past o v), split into the operand format; (alpha, beta) = (2, -1)
+// gives t~ = 2 t - t^T, (1, 0) the amplitudes
 template <typename T>
 __global__ void k_pack_pairmat(const double* __restrict__ t2, int o, int v, double alpha, double beta,
-                               T* __restrict__ P, int64_t ld, int64_t piece) {
+                               T* __restrict__ P, int64_t ld, int64_t piece, const double* __restrict__ u2 = nullptr,
+                               double gamma = 0.0, double delta = 0.0) {
   const int64_t ov = static_cast<int64_t>(o) * v, vv = static_cast<int64_t>(v) * v;
   const int64_t r = blockIdx.x;  // (i, c)
   const int i = static_cast<int>(r / v), c = static_cast<int>(r % v);
@@ -475,10 +477,55 @@ __global__ void k_pack_pairmat(const double* __restrict__ t2, int o, int v, doub
     double x = 0.0;
     if (k < ov) {
       const int m = static_cast<int>(k / v), b = static_cast<int>(k % v);
-      x = alpha * t2[(static_cast<int64_t>(i) * o + m) * vv + static_cast<int64_t>(c) * v + b] +
-          beta * t2[(static_cast<int64_t>(m) * o + i) * vv + static_cast<int64_t>(c) * v + b];
+      const int64_t e1 = (static_cast<int64_t>(i) * o + m) * vv + static_cast<int64_t>(c) * v + b;
+      const int64_t e2 = (static_cast<int64_t>(m) * o + i) * vv + static_cast<int64_t>(c) * v + b;
+      x = alpha * t2[e1] + beta * t2[e2];
+      if (u2) x += gamma * u2[e1] + delta * u2[e2];
     }
     Store<T>::put(P, r * ld + k, piece, x, 1.f);
+  }
+}
+
+// A strided 4-D view of an FP64 array: element (r1, r2, k1, k2) at
+// p[r1*sr1 + r2*sr2 + k1*sk1 + k2*sk2], times coef (p null: the view is 0).
+struct View {
+  const double* p;
+  int64_t sr1, sr2, sk1, sk2;
+  double coef;
+};
+
+// Contraction operand from up to two views: out[r][k] = v1(r, k) + v2(r, k),
+// r = r1*R2 + r2 (row), k = k1*K2 + k2 (reduction index, contiguous), zero for
+// k >= K1*K2 up to the row pitch ld; written in the operand format.
+template <typename T>
+__global__ void k_pack_view(View v1, View v2, int64_t R1, int64_t R2, int64_t K1, int64_t K2, T* __restrict__ out,
+                            int64_t ld, int64_t piece) {
+  const int64_t total = R1 * R2 * ld, K = K1 * K2;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = q / ld, k = q % ld;
+    double x = 0.0;
+    if (k < K) {
+      const int64_t r1 = r / R2, r2 = r % R2, k1 = k / K2, k2 = k % K2;
+      x = v1.coef * v1.p[r1 * v1.sr1 + r2 * v1.sr2 + k1 * v1.sk1 + k2 * v1.sk2];
+      if (v2.p) x += v2.coef * v2.p[r1 * v2.sr1 + r2 * v2.sr2 + k1 * v2.sk1 + k2 * v2.sk2];
+    }
+    Store<T>::put(out, q, piece, x, 1.f);
+  }
+}
+
+// dst[n*sdn + m*sdm] (= | +=) alpha * src[n*ldo + m] for m < M, n < N: a
+// contraction output (float-float or FP64) into a strided FP64 array
+template <typename S>
+__global__ void k_out_view(const S* __restrict__ src, int64_t ldo, int64_t M, int64_t N, double alpha,
+                           double* __restrict__ dst, int64_t sdn, int64_t sdm, int accumulate) {
+  const int64_t total = M * N;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t n = q / M, m = q % M;
+    const double x = alpha * Ar<S>::to_d(src[n * ldo + m]);
+    double* d = dst + n * sdn + m * sdm;
+    *d = accumulate ? *d + x : x;
   }
 }
 
@@ -499,6 +546,14 @@ __global__ void k_to_f64_scaled(const S* __restrict__ in, double* __restrict__ o
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x)
     out[k] = scale * Ar<S>::to_d(in[k]);
+}
+
+// x[k] *= factor * (*g)  (g: a device scalar, e.g. the incoming gradient of E)
+__global__ void k_scale_by(double* __restrict__ x, int64_t n, double factor, const double* __restrict__ g) {
+  const double f = factor * (g ? *g : 1.0);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[k] *= f;
 }
 
 __global__ void k_debug_wait(const int* flag, unsigned long long timeout_ns, Status* st) {
@@ -634,14 +689,20 @@ struct Plan {
   std::vector<PBlock> pbs;
   int64_t maxpairs = 0, maxrows = 0, ldO = 0, ldt = 0;
   int64_t n_epart = 0;
-  // byte offsets into the workspace; 0 = not present (offset 0 is the status header)
-  size_t o_LT = 0, o_LN = 0, o_tp = 0, o_tm = 0, o_tpT = 0, o_tmT = 0, o_bp = 0, o_bm = 0;
-  size_t o_G = 0, o_gp = 0, o_gm = 0, o_Op = 0, o_Om = 0, o_Gp = 0, o_Gm = 0, o_Gt = 0, o_Gb = 0, o_E = 0;
-  size_t o_D = 0;
-  size_t total = 0;
+  // Byte offsets inside the system's region (operands prepared once per call,
+  // the D accumulator and the E partials) and inside a scratch slot (the
+  // intermediates of one pair block in flight).  0 = not present.
+  size_t s_scl = 0;  // FP16 path: operand bounds (8 x u32) at +0, scales (5 floats) at +64 (always present)
+  size_t s_tp = 0, s_tm = 0, s_LT = 0, s_LN = 0, s_tpT = 0, s_tmT = 0, s_bp = 0, s_bm = 0, s_D = 0, s_E = 0;
+  // A scratch slot has two parts: operand pieces (g+-, the Gamma slabs) first, then float-float (or
+  // FP64) scratch (G, Omega+-, Gamma+-).  Slot offsets are relative to the start of their part.
+  size_t k_gp = 0, k_gm = 0, k_Gt = 0, k_Gb = 0;               // piece part
+  size_t k_G = 0, k_Op = 0, k_Om = 0, k_Gp = 0, k_Gm = 0;      // scratch part
+  size_t sys_bytes = 0, piece_bytes = 0, scratch_bytes = 0;
 };
 
 constexpr size_t kStatusBytes = 256;
+constexpr int kBatchSlots = 8;  // pair blocks of different systems in flight at once (batched schedule)
 
 static int env_int(const char* name, int dflt) {
   const char* s = std::getenv(name);
@@ -694,50 +755,58 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
 
   const bool res = which & (CC_WS_RESIDUAL | CC_WS_LAGRANGIAN);
   const bool den = which & CC_WS_DENSITY;
-  size_t cur = kStatusBytes;
-  auto take = [&](size_t bytes) {
+  // every region starts past a 256-byte gap, so that offset 0 means "not present" in each
+  size_t sys = 256, pcs = 256, scr = 256;
+  auto take = [](size_t& cur, size_t bytes) {
     const size_t at = cur;
     cur += rup(static_cast<int64_t>(bytes), 256);
     return at;
   };
   const int pr = prec;
-  P.o_tp = take(mat_bytes(pr, P.Pop, P.Kvp));
-  P.o_tm = take(mat_bytes(pr, P.Pom, P.Kvm));
+  P.s_scl = take(sys, 256);  // = 256
+  P.s_tp = take(sys, mat_bytes(pr, P.Pop, P.Kvp));
+  P.s_tm = take(sys, mat_bytes(pr, P.Pom, P.Kvm));
   if (res) {
-    P.o_LT = take(mat_bytes(pr, v * v, P.Kj));
-    P.o_G = take(static_cast<size_t>(P.maxrows) * P.maxrows * 8);
-    P.o_gp = take(mat_bytes(pr, P.maxpairs, P.Kvp));
-    P.o_gm = take(mat_bytes(pr, P.maxpairs, P.Kvm));
-    P.o_Op = take(static_cast<size_t>(P.Pop) * P.ldO * 8);
-    P.o_Om = take(static_cast<size_t>(P.Pom) * P.ldO * 8);
+    P.s_LT = take(sys, mat_bytes(pr, v * v, P.Kj));
+    P.k_G = take(scr, static_cast<size_t>(P.maxrows) * P.maxrows * 8);
+    P.k_gp = take(pcs, mat_bytes(pr, P.maxpairs, P.Kvp));
+    P.k_gm = take(pcs, mat_bytes(pr, P.maxpairs, P.Kvm));
+    P.k_Op = take(scr, static_cast<size_t>(P.Pop) * P.ldO * 8);
+    P.k_Om = take(scr, static_cast<size_t>(P.Pom) * P.ldO * 8);
   }
   if (den) {
-    P.o_LN = take(mat_bytes(pr, nj, v * P.vp));
-    P.o_tpT = take(mat_bytes(pr, P.Pvp, P.Kop));
-    P.o_tmT = take(mat_bytes(pr, P.Pvm, P.Kom));
-    P.o_bp = take(mat_bytes(pr, P.Pvp, P.Kop));
-    P.o_bm = take(mat_bytes(pr, P.Pvp, P.Kom));
-    P.o_Gp = take(static_cast<size_t>(P.maxpairs) * P.Kvp * 8);
-    P.o_Gm = take(static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
-    P.o_Gt = take(mat_bytes(pr, P.maxrows, P.ldt));
-    P.o_Gb = take(mat_bytes(pr, P.maxrows, P.ldt));
-    if (prec != CC_PREC_FP64) P.o_D = take(static_cast<size_t>(nj) * v * v * 8);  // float-float D
+    P.s_LN = take(sys, mat_bytes(pr, nj, v * P.vp));
+    P.s_tpT = take(sys, mat_bytes(pr, P.Pvp, P.Kop));
+    P.s_tmT = take(sys, mat_bytes(pr, P.Pvm, P.Kom));
+    P.s_bp = take(sys, mat_bytes(pr, P.Pvp, P.Kop));
+    P.s_bm = take(sys, mat_bytes(pr, P.Pvp, P.Kom));
+    if (prec != CC_PREC_FP64) P.s_D = take(sys, static_cast<size_t>(nj) * v * v * 8);  // float-float D
+    P.k_Gp = take(scr, static_cast<size_t>(P.maxpairs) * P.Kvp * 8);
+    P.k_Gm = take(scr, static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
+    P.k_Gt = take(pcs, mat_bytes(pr, P.maxrows, P.ldt));
+    P.k_Gb = take(pcs, mat_bytes(pr, P.maxrows, P.ldt));
   }
-  P.o_E = take(static_cast<size_t>(P.n_epart) * 8);
-  P.total = cur;
+  P.s_E = take(sys, static_cast<size_t>(P.n_epart) * 8);
+  P.sys_bytes = sys;
+  P.piece_bytes = pcs;
+  P.scratch_bytes = scr;
   return true;
 }
 
 // ---------------------------------------------------------------------------
 // execution
 // ---------------------------------------------------------------------------
+// Workspace header (the first kStatusBytes bytes): the latched Status at 0,
+// the FP16 path's operand bounds at 64 and scales at 128, the contraction's
+// tile-queue counter at kQueueOffset.
+constexpr size_t kQueueOffset = 224;
+
 struct Ctx {
   cudaStream_t st;
   Status* status;
+  int* queue = nullptr;  // tile counter of the mixed contraction launches
   uint64_t timeout_ns;
   bool adjoint = false;  // residual of tbar2 with L^J transposed: sum_ab tbar_ij^ab g_acbd
-  const double* r2 = nullptr;  // excited-state density: the ladder doubles are r0 t2 + r2
-  double r0 = 1.0;
   int err = 0;
   void check(int rc) {
     if (rc && !err) err = rc;
@@ -776,7 +845,7 @@ struct Profiler {
 static Profiler g_prof;
 
 template <typename F>
-static int profiled(const GemmOp& g, cudaStream_t s, F&& launch, const GemmOp* g2) {
+static int profiled(const GemmOp* ops, int nops, cudaStream_t s, F&& launch) {
   bool on;
   {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -789,8 +858,8 @@ static int profiled(const GemmOp& g, cudaStream_t s, F&& launch, const GemmOp* g
     e0 = g_prof.get();
     e1 = g_prof.get();
     g_prof.pending.emplace_back(e0, e1);
-    g_prof.flops += 2.0 * static_cast<double>(g.M) * static_cast<double>(g.N) * static_cast<double>(g.K);
-    if (g2) g_prof.flops += 2.0 * static_cast<double>(g2->M) * static_cast<double>(g2->N) * static_cast<double>(g2->K);
+    for (int i = 0; i < nops; ++i)
+      g_prof.flops += 2.0 * static_cast<double>(ops[i].M) * static_cast<double>(ops[i].N) * static_cast<double>(ops[i].K);
     g_prof.launches += 1;
   }
   cudaEventRecord(e0, s);
@@ -848,16 +917,18 @@ static int64_t f64_kchunk(int64_t M, int64_t N, int64_t K) {
   return std::max<int64_t>(32, rup((K + splits - 1) / splits, 32));
 }
 
-// Launch one group of up to two contractions of the same shape class.
+// Launch one group of independent contractions (one persistent launch on the
+// mixed paths, one launch each on the FP64 path).
 template <typename T>
 static void run_gemms(const Gm* g, int n, Ctx& c) {
+  if (n <= 0) return;
   std::vector<GemmOp> ops(n);
   for (int i = 0; i < n; ++i) {
     GemmOp& o = ops[i];
     o.A = g[i].A; o.lda = g[i].lda; o.a_rows = g[i].a_rows; o.a_cols = g[i].a_cols; o.a_piece = g[i].a_piece;
     o.B = g[i].B; o.ldb = g[i].ldb; o.b_rows = g[i].b_rows; o.b_cols = g[i].b_cols; o.b_piece = g[i].b_piece;
     o.M = g[i].M; o.N = g[i].N; o.K = g[i].K; o.out = g[i].out; o.ldo = g[i].ldo; o.tri = g[i].tri;
-    o.status = c.status; o.timeout_ns = c.timeout_ns;
+    o.status = c.status; o.queue = c.queue; o.timeout_ns = c.timeout_ns;
   }
   if (Path<T>::mixed) {
     for (int i = 0; i < n; ++i) {
@@ -866,7 +937,7 @@ static void run_gemms(const Gm* g, int n, Ctx& c) {
       ops[i].scale_a = g[i].sa;
       ops[i].scale_b = g[i].sb;
     }
-    c.check(profiled(ops[0], c.st, [&] { return gemm_mixed(ops.data(), n, c.st); }, n > 1 ? &ops[1] : nullptr));
+    c.check(profiled(ops.data(), n, c.st, [&] { return gemm_mixed(ops.data(), n, c.st); }));
   } else {
     for (int i = 0; i < n; ++i) {
       GemmOp& o = ops[i];
@@ -875,176 +946,328 @@ static void run_gemms(const Gm* g, int n, Ctx& c) {
       if (split && !g[i].acc)
         c.cuda(cudaMemsetAsync(o.out, 0, static_cast<size_t>(o.N) * o.ldo * sizeof(double), c.st));
       o.mode = (split || g[i].acc) ? OUT_F64_ATOMIC : OUT_F64_STORE;
-      c.check(profiled(o, c.st, [&] { return gemm_f64(o, c.st); }, nullptr));
+      c.check(profiled(&o, 1, c.st, [&] { return gemm_f64(o, c.st); }));
     }
   }
 }
 
+// One system of a call: its plan, its workspace region and its outputs.
+struct SysRun {
+  const cc_ladder_system* sy = nullptr;
+  Plan P;
+  char* base = nullptr;  // the system's region of the workspace
+  double* omega = nullptr;
+  double* D = nullptr;
+  double* E = nullptr;
+  const double* r2 = nullptr;  // excited-state density: the ladder doubles are r0 t2 + r2
+  double r0 = 1.0;
+  size_t next = 0;             // next pair block to schedule
+  double left = 0.0;           // counted flops of the pair blocks not yet scheduled
+  std::vector<size_t> subset;  // non-empty: only these pair blocks (a shard of the system)
+};
+
+// One pair block in flight: the system, the block, the scratch slot it uses
+// (its operand-piece part and its float-float scratch part).
+struct Slot {
+  char* pieces;
+  char* scratch;
+};
+struct Item {
+  SysRun* r;
+  size_t ib;
+  Slot slot;
+};
+
 template <typename T>
-static void run_system(const cc_ladder_system& sy, const Plan& P, char* ws, double* omega, double* D, double* E,
-                       bool do_res, bool do_den, bool do_E, Ctx& c) {
+struct Ptrs {
   using S = typename Path<T>::S;
+  T *tp, *tm, *LT, *LN, *tpT, *tmT, *bp, *bm;
+  S *Dacc;
+  double* epart;
+  unsigned* bnd;
+  float* scl;
+  int64_t tp_piece, tm_piece, LT_piece, LN_piece, tpT_piece, tmT_piece, bp_piece, bm_piece;
+  Ptrs(const SysRun& R) {
+    const Plan& P = R.P;
+    char* w = R.base;
+    auto opt = [&](size_t off) { return off ? w + off : nullptr; };
+    tp = reinterpret_cast<T*>(opt(P.s_tp));
+    tm = reinterpret_cast<T*>(opt(P.s_tm));
+    LT = reinterpret_cast<T*>(opt(P.s_LT));
+    LN = reinterpret_cast<T*>(opt(P.s_LN));
+    tpT = reinterpret_cast<T*>(opt(P.s_tpT));
+    tmT = reinterpret_cast<T*>(opt(P.s_tmT));
+    bp = reinterpret_cast<T*>(opt(P.s_bp));
+    bm = reinterpret_cast<T*>(opt(P.s_bm));
+    // D accumulates over pair blocks in float-float scratch (mixed) or directly in the FP64 output
+    Dacc = Path<T>::mixed ? reinterpret_cast<S*>(opt(P.s_D)) : reinterpret_cast<S*>(R.D);
+    epart = reinterpret_cast<double*>(w + P.s_E);
+    bnd = reinterpret_cast<unsigned*>(w + P.s_scl);
+    scl = reinterpret_cast<float*>(w + P.s_scl + 64);
+    const int64_t vv = static_cast<int64_t>(P.v) * P.v;
+    tp_piece = P.Pop * P.Kvp;
+    tm_piece = P.Pom * P.Kvm;
+    LT_piece = vv * P.Kj;
+    LN_piece = static_cast<int64_t>(P.nj) * P.v * P.vp;
+    tpT_piece = P.Pvp * P.Kop;
+    tmT_piece = P.Pvm * P.Kom;
+    bp_piece = P.Pvp * P.Kop;
+    bm_piece = P.Pvp * P.Kom;
+  }
+  // operand scales of the FP16 two-piece path, else null
+  const float* SC(int i) const { return std::is_same<T, __half>::value ? scl + i : nullptr; }
+};
+
+// Once per system and call: operand scales (FP16 path), tau^pm, L in both
+// layouts, the transposed tau^pm and the tbar^pm rows; zeroed D accumulator.
+template <typename T>
+static void prep_system(const SysRun& R, bool do_res, bool do_den, Ctx& c) {
+  const cc_ladder_system& sy = *R.sy;
+  const Plan& P = R.P;
+  const Ptrs<T> X(R);
   const int o = P.o, v = P.v, nj = P.nj, vp = P.vp;
   const int64_t vv = static_cast<int64_t>(v) * v;
   const int minus = P.minus;
   cudaStream_t st = c.st;
-  T* tp = at<T>(ws, P.o_tp);
-  T* tm = at<T>(ws, P.o_tm);
-  const int64_t tp_piece = P.Pop * P.Kvp, tm_piece = P.Pom * P.Kvm;
-
-  // --- operand scales of the FP16 two-piece path (device-side, no host sync)
-  constexpr bool scaled = std::is_same<T, __half>::value;
-  unsigned* bnd = reinterpret_cast<unsigned*>(ws + 64);
-  float* scl = reinterpret_cast<float*>(ws + 128);
-  auto SC = [&](int i) -> const float* { return scaled ? scl + i : nullptr; };
-  if (scaled) {
+  if (std::is_same<T, __half>::value) {
+    // device-side bounds and scales, no host synchronisation
     const double* amp = c.adjoint ? sy.tbar2 : sy.t2;
-    c.cuda(cudaMemsetAsync(bnd, 0, 8 * sizeof(unsigned), st));
-    k_bound_L<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(sy.L_vv, nj, vv, bnd);
+    c.cuda(cudaMemsetAsync(X.bnd, 0, 8 * sizeof(unsigned), st));
+    k_bound_L<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(sy.L_vv, nj, vv, X.bnd);
     k_bound_amp<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(
-        c.adjoint ? nullptr : sy.t1, amp, o, v, bnd + 2, c.r2, c.r0);
+        c.adjoint ? nullptr : sy.t1, amp, o, v, X.bnd + 2, R.r2, R.r0);
     c.launched(2);
     if (do_den) {
       k_bound_amp<<<static_cast<unsigned>(std::min<int64_t>(4096, (vv + 255) / 256)), 256, 0, st>>>(
-          nullptr, sy.tbar2, o, v, bnd + 4);
+          nullptr, sy.tbar2, o, v, X.bnd + 4);
       c.launched();
     }
-    k_scales<<<1, 1, 0, st>>>(bnd, scl);
+    k_scales<<<1, 1, 0, st>>>(X.bnd, X.scl);
     c.launched();
   }
-
-  // --- tau^pm (both directions need it)
-  c.cuda(cudaMemsetAsync(tp, 0, mat_bytes(P.prec, P.Pop, P.Kvp), st));
-  if (minus) c.cuda(cudaMemsetAsync(tm, 0, mat_bytes(P.prec, P.Pom, P.Kvm), st));
+  // tau^pm (both directions need it)
+  c.cuda(cudaMemsetAsync(X.tp, 0, mat_bytes(P.prec, P.Pop, P.Kvp), st));
+  if (minus) c.cuda(cudaMemsetAsync(X.tm, 0, mat_bytes(P.prec, P.Pom, P.Kvm), st));
   k_pack_tau<T><<<dim3(v, static_cast<unsigned>(P.Pop)), 128, 0, st>>>(
-      c.adjoint ? nullptr : sy.t1, c.adjoint ? sy.tbar2 : sy.t2, o, v, tp, P.Kvp, tp_piece, tm, P.Kvm, tm_piece,
-      minus, SC(1), c.r2, c.r0);
+      c.adjoint ? nullptr : sy.t1, c.adjoint ? sy.tbar2 : sy.t2, o, v, X.tp, P.Kvp, X.tp_piece, X.tm, P.Kvm,
+      X.tm_piece, minus, X.SC(1), R.r2, R.r0);
   c.launched();
-
-  double* epart = at<double>(ws, P.o_E);
-  const int64_t o2 = static_cast<int64_t>(o) * o;
-
-  // --- residual-side preparation
-  T *LT = nullptr, *gp = nullptr, *gm = nullptr;
-  S *G = nullptr, *Op = nullptr, *Om = nullptr;
-  const int64_t LT_piece = vv * P.Kj, g_piece_p = P.maxpairs * P.Kvp, g_piece_m = P.maxpairs * P.Kvm;
   if (do_res) {
-    LT = at<T>(ws, P.o_LT);
-    G = at<S>(ws, P.o_G);
-    gp = at<T>(ws, P.o_gp);
-    gm = at<T>(ws, P.o_gm);
-    Op = at<S>(ws, P.o_Op);
-    Om = at<S>(ws, P.o_Om);
     k_prep_LT<T><<<dim3(static_cast<unsigned>((vv + 31) / 32), static_cast<unsigned>(P.Kj / 32)), dim3(32, 8), 0,
-                   st>>>(sy.L_vv, nj, vv, v, c.adjoint ? 1 : 0, LT, P.Kj, LT_piece, SC(0));
+                   st>>>(sy.L_vv, nj, vv, v, c.adjoint ? 1 : 0, X.LT, P.Kj, X.LT_piece, X.SC(0));
     c.launched();
-    c.cuda(cudaMemsetAsync(gp, 0, mat_bytes(P.prec, P.maxpairs, P.Kvp), st));
-    if (minus) c.cuda(cudaMemsetAsync(gm, 0, mat_bytes(P.prec, P.maxpairs, P.Kvm), st));
   }
-
-  // --- density-side preparation
-  T *LN = nullptr, *tpT = nullptr, *tmT = nullptr, *bp = nullptr, *bm = nullptr, *Gt = nullptr, *Gb = nullptr;
-  S *Gp = nullptr, *Gm_ = nullptr, *Dacc = nullptr;
-  const int64_t LN_piece = static_cast<int64_t>(nj) * v * vp;
-  const int64_t tpT_piece = P.Pvp * P.Kop, tmT_piece = P.Pvm * P.Kom;
-  const int64_t bp_piece = P.Pvp * P.Kop, bm_piece = P.Pvp * P.Kom;
-  const int64_t gt_piece = P.maxrows * P.ldt;
   if (do_den) {
-    LN = at<T>(ws, P.o_LN);
-    tpT = at<T>(ws, P.o_tpT);
-    tmT = at<T>(ws, P.o_tmT);
-    bp = at<T>(ws, P.o_bp);
-    bm = at<T>(ws, P.o_bm);
-    Gp = at<S>(ws, P.o_Gp);
-    Gm_ = at<S>(ws, P.o_Gm);
-    Gt = at<T>(ws, P.o_Gt);
-    Gb = at<T>(ws, P.o_Gb);
-    // D accumulates over pair blocks: in float-float scratch (mixed) or
-    // directly in the FP64 output (FP64 path)
-    Dacc = Path<T>::mixed ? at<S>(ws, P.o_D) : reinterpret_cast<S*>(D);
-    k_prep_LN<T><<<2048, 256, 0, st>>>(sy.L_vv, nj, v, vp, LN, LN_piece, SC(0));
+    k_prep_LN<T><<<2048, 256, 0, st>>>(sy.L_vv, nj, v, vp, X.LN, X.LN_piece, X.SC(0));
     c.launched();
-    c.cuda(cudaMemsetAsync(tpT, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
+    c.cuda(cudaMemsetAsync(X.tpT, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
     k_transpose<T, Path<T>::NP><<<dim3(static_cast<unsigned>((P.Pvp + 31) / 32), static_cast<unsigned>((P.Pop + 31) / 32)),
-                                  dim3(32, 8), 0, st>>>(tp, P.Pop, P.Pvp, P.Kvp, tp_piece, tpT, P.Kop, tpT_piece);
+                                  dim3(32, 8), 0, st>>>(X.tp, P.Pop, P.Pvp, P.Kvp, X.tp_piece, X.tpT, P.Kop, X.tpT_piece);
     c.launched();
-    c.cuda(cudaMemsetAsync(bp, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
+    c.cuda(cudaMemsetAsync(X.bp, 0, mat_bytes(P.prec, P.Pvp, P.Kop), st));
     if (minus) {
-      c.cuda(cudaMemsetAsync(tmT, 0, mat_bytes(P.prec, P.Pvm, P.Kom), st));
+      c.cuda(cudaMemsetAsync(X.tmT, 0, mat_bytes(P.prec, P.Pvm, P.Kom), st));
       k_transpose<T, Path<T>::NP><<<dim3(static_cast<unsigned>((P.Pvm + 31) / 32), static_cast<unsigned>((P.Pom + 31) / 32)),
-                                    dim3(32, 8), 0, st>>>(tm, P.Pom, P.Pvm, P.Kvm, tm_piece, tmT, P.Kom, tmT_piece);
+                                    dim3(32, 8), 0, st>>>(X.tm, P.Pom, P.Pvm, P.Kvm, X.tm_piece, X.tmT, P.Kom, X.tmT_piece);
       c.launched();
-      c.cuda(cudaMemsetAsync(bm, 0, mat_bytes(P.prec, P.Pvp, P.Kom), st));
+      c.cuda(cudaMemsetAsync(X.bm, 0, mat_bytes(P.prec, P.Pvp, P.Kom), st));
     }
     for (const PBlock& b : P.pbs) {
       k_pack_tbar<T><<<static_cast<unsigned>(b.npairs), 128, 0, st>>>(sy.tbar2, o, v, b.a0, b.b0, b.nb, b.diag,
-                                                                     b.pair_off, bp, P.Kop, bp_piece, bm, P.Kom,
-                                                                     bm_piece, minus, SC(2));
+                                                                     b.pair_off, X.bp, P.Kop, X.bp_piece, X.bm, P.Kom,
+                                                                     X.bm_piece, minus, X.SC(2));
       c.launched();
     }
-    c.cuda(cudaMemsetAsync(Gt, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
-    c.cuda(cudaMemsetAsync(Gb, 0, mat_bytes(P.prec, P.maxrows, P.ldt), st));
-    c.cuda(cudaMemsetAsync(Dacc, 0, static_cast<size_t>(nj) * vv * 8, st));
+    c.cuda(cudaMemsetAsync(X.Dacc, 0, static_cast<size_t>(nj) * vv * 8, st));
   }
+  // a shard writes the E partials of its own pair blocks only: the others count as zero
+  if (!R.subset.empty()) c.cuda(cudaMemsetAsync(X.epart, 0, static_cast<size_t>(P.n_epart) * 8, st));
+}
 
-  const unsigned ntp = static_cast<unsigned>(P.nt * (P.nt + 1) / 2);
-  for (size_t ib = 0; ib < P.pbs.size() && !c.err; ++ib) {
-    const PBlock& b = P.pbs[ib];
+// The pair blocks of one wave (at most one per system, each with its own
+// scratch slot) through the four contractions.  Two grouped contraction
+// launches carry every block of the wave: the g-builds with the Gamma+-
+// contractions (independent), then the ladders +- with the D slabs
+// (independent); the pack / unpack passes of each block sit between them.
+template <typename T>
+static void run_wave(const std::vector<Item>& items, bool do_res, bool do_den, bool do_E, Ctx& c) {
+  using S = typename Path<T>::S;
+  cudaStream_t st = c.st;
+  std::vector<Gm> first, second;
+  // scratch of an item: slot-part-relative offsets from its own plan
+  auto K = [](const Item& it, size_t off) { return off ? it.slot.scratch + off : nullptr; };
+  auto Q = [](const Item& it, size_t off) { return off ? it.slot.pieces + off : nullptr; };
+  for (const Item& it : items) {
+    const Plan& P = it.r->P;
+    const Ptrs<T> X(*it.r);
+    const PBlock& b = P.pbs[it.ib];
+    const int v = P.v;
+    const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
     if (do_res) {
       // g-build: G[(b_l,d)][(a_l,c)] = sum_J L^J_ac L^J_bd
-      const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
-      const Gm g = {LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, LT_piece,
-                    LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, LT_piece,
-                    M, N, P.Kj, G, M, false, SC(0), SC(0), b.diag ? v : 0};  // diagonal block: pairs a <= b only
-      run_gemms<T>(&g, 1, c);
+      first.push_back({X.LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, X.LT_piece,
+                       X.LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, X.LT_piece,
+                       M, N, P.Kj, K(it, P.k_G), M, false, X.SC(0), X.SC(0), b.diag ? v : 0});  // diagonal block: a <= b
+    }
+    if (do_den) {
+      // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]
+      first.push_back({X.tpT, P.Kop, P.Pvp, P.Kop, X.tpT_piece, X.bp + b.pair_off * P.Kop, P.Kop, b.npairs, P.Kop,
+                       X.bp_piece, P.Pvp, b.npairs, P.Kop, K(it, P.k_Gp), P.Kvp, false, X.SC(1), X.SC(2)});
+      if (P.minus)
+        first.push_back({X.tmT, P.Kom, P.Pvm, P.Kom, X.tmT_piece, X.bm + b.pair_off * P.Kom, P.Kom, b.npairs, P.Kom,
+                         X.bm_piece, P.Pvm, b.npairs, P.Kom, K(it, P.k_Gm), P.Kvm, false, X.SC(1), X.SC(2)});
+    }
+  }
+  run_gemms<T>(first.data(), static_cast<int>(first.size()), c);
+  if (c.err) return;  // nothing more is launched after a refused or failed launch
+  for (const Item& it : items) {
+    const Plan& P = it.r->P;
+    const Ptrs<T> X(*it.r);
+    const PBlock& b = P.pbs[it.ib];
+    const int v = P.v;
+    const unsigned ntp = static_cast<unsigned>(P.nt * (P.nt + 1) / 2);
+    const int64_t gpiece_p = P.maxpairs * P.Kvp, gpiece_m = P.maxpairs * P.Kvm, gt_piece = P.maxrows * P.ldt;
+    if (do_res) {
       k_pack_g<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
-          G, M, v, b.a0, b.b0, b.nb, b.diag, P.nt, gp, P.Kvp, g_piece_p, gm, P.Kvm, g_piece_m, minus, SC(3));
-      c.launched();
-      // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]  (both signs in one launch)
-      const Gm lg[2] = {
-          {gp, P.Kvp, b.npairs, P.Kvp, g_piece_p, tp, P.Kvp, P.Pop, P.Kvp, tp_piece, b.npairs, P.Pop, P.Kvp, Op,
-           P.ldO, false, SC(3), SC(1)},
-          {gm, P.Kvm, b.npairs, P.Kvm, g_piece_m, tm, P.Kvm, P.Pom, P.Kvm, tm_piece, b.npairs, P.Pom, P.Kvm, Om,
-           P.ldO, false, SC(3), SC(1)}};
-      run_gemms<T>(lg, minus ? 2 : 1, c);
-      k_unpack_omega<S><<<static_cast<unsigned>(o2), 256, 0, st>>>(
-          Op, Om, P.ldO, o, v, b.a0, b.b0, b.nb, b.diag, b.npairs, minus, omega, sy.tbar2,
-          do_E ? epart + static_cast<int64_t>(ib) * o2 : nullptr);
+          reinterpret_cast<const S*>(K(it, P.k_G)), static_cast<int64_t>(b.na) * v, v, b.a0, b.b0, b.nb, b.diag,
+          P.nt, reinterpret_cast<T*>(Q(it, P.k_gp)), P.Kvp, gpiece_p, reinterpret_cast<T*>(Q(it, P.k_gm)), P.Kvm,
+          gpiece_m, P.minus, X.SC(3));
       c.launched();
     }
     if (do_den) {
-      // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]  (both signs in one launch)
-      const Gm gg[2] = {
-          {tpT, P.Kop, P.Pvp, P.Kop, tpT_piece, bp + b.pair_off * P.Kop, P.Kop, b.npairs, P.Kop, bp_piece, P.Pvp,
-           b.npairs, P.Kop, Gp, P.Kvp, false, SC(1), SC(2)},
-          {tmT, P.Kom, P.Pvm, P.Kom, tmT_piece, bm + b.pair_off * P.Kom, P.Kom, b.npairs, P.Kom, bm_piece, P.Pvm,
-           b.npairs, P.Kom, Gm_, P.Kvm, false, SC(1), SC(2)}};
-      run_gemms<T>(gg, minus ? 2 : 1, c);
       k_unpack_gamma<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
-          Gp, Gm_, P.Kvp, P.Kvm, v, vp, b.a0, b.b0, b.nb, b.diag, P.nt, minus, Gt, P.ldt, gt_piece, Gb, P.ldt,
-          gt_piece, SC(4));
+          reinterpret_cast<const S*>(K(it, P.k_Gp)), reinterpret_cast<const S*>(K(it, P.k_Gm)), P.Kvp, P.Kvm, v, P.vp,
+          b.a0, b.b0, b.nb, b.diag, P.nt, P.minus, reinterpret_cast<T*>(Q(it, P.k_Gt)), P.ldt, gt_piece,
+          reinterpret_cast<T*>(Q(it, P.k_Gb)), P.ldt, gt_piece, X.SC(4));
       c.launched();
+    }
+  }
+  for (const Item& it : items) {
+    const Plan& P = it.r->P;
+    const Ptrs<T> X(*it.r);
+    const PBlock& b = P.pbs[it.ib];
+    const int v = P.v, vp = P.vp, nj = P.nj;
+    const int64_t vv = static_cast<int64_t>(v) * v;
+    const int64_t gpiece_p = P.maxpairs * P.Kvp, gpiece_m = P.maxpairs * P.Kvm, gt_piece = P.maxrows * P.ldt;
+    if (do_res) {
+      // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]
+      // (the g+- maps end at the last virtual pair: columns up to the padded K read as zero)
+      second.push_back({Q(it, P.k_gp), P.Kvp, b.npairs, P.Pvp, gpiece_p, X.tp, P.Kvp, P.Pop, P.Kvp, X.tp_piece,
+                        b.npairs, P.Pop, P.Kvp, K(it, P.k_Op), P.ldO, false, X.SC(3), X.SC(1)});
+      if (P.minus)
+        second.push_back({Q(it, P.k_gm), P.Kvm, b.npairs, P.Pvm, gpiece_m, X.tm, P.Kvm, P.Pom, P.Kvm, X.tm_piece,
+                          b.npairs, P.Pom, P.Kvm, K(it, P.k_Om), P.ldO, false, X.SC(3), X.SC(1)});
+    }
+    if (do_den) {
       // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd  (top and, off the diagonal, bottom)
       const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 64);
       const int64_t Mb = static_cast<int64_t>(b.nb) * v, Kb = rup(static_cast<int64_t>(b.na) * vp, 64);
-      const Gm dg[2] = {
-          {Gt, P.ldt, Mt, P.ldt, gt_piece, LN + static_cast<int64_t>(b.b0) * vp, static_cast<int64_t>(v) * vp, nj,
-           static_cast<int64_t>(v - b.b0) * vp, LN_piece, Mt, nj, Kt, Dacc + static_cast<int64_t>(b.a0) * v, vv,
-           true, SC(4), SC(0)},
-          {Gb, P.ldt, Mb, P.ldt, gt_piece, LN + static_cast<int64_t>(b.a0) * vp, static_cast<int64_t>(v) * vp, nj,
-           static_cast<int64_t>(v - b.a0) * vp, LN_piece, Mb, nj, Kb, Dacc + static_cast<int64_t>(b.b0) * v, vv,
-           true, SC(4), SC(0)}};
-      run_gemms<T>(dg, b.diag ? 1 : 2, c);
+      // (the slab maps end at the block's last column: the rest of the padded K reads as zero)
+      second.push_back({Q(it, P.k_Gt), P.ldt, Mt, static_cast<int64_t>(b.nb) * vp, gt_piece,
+                        X.LN + static_cast<int64_t>(b.b0) * vp,
+                        static_cast<int64_t>(v) * vp, nj, static_cast<int64_t>(v - b.b0) * vp, X.LN_piece, Mt, nj,
+                        Kt, X.Dacc + static_cast<int64_t>(b.a0) * v, vv, true, X.SC(4), X.SC(0)});
+      if (!b.diag)
+        second.push_back({Q(it, P.k_Gb), P.ldt, Mb, static_cast<int64_t>(b.na) * vp, gt_piece,
+                          X.LN + static_cast<int64_t>(b.a0) * vp,
+                          static_cast<int64_t>(v) * vp, nj, static_cast<int64_t>(v - b.a0) * vp, X.LN_piece, Mb,
+                          nj, Kb, X.Dacc + static_cast<int64_t>(b.b0) * v, vv, true, X.SC(4), X.SC(0)});
     }
   }
+  run_gemms<T>(second.data(), static_cast<int>(second.size()), c);
+  if (c.err || !do_res) return;
+  for (const Item& it : items) {
+    const Plan& P = it.r->P;
+    const Ptrs<T> X(*it.r);
+    const PBlock& b = P.pbs[it.ib];
+    const int64_t o2 = static_cast<int64_t>(P.o) * P.o;
+    k_unpack_omega<S><<<static_cast<unsigned>(o2), 256, 0, st>>>(
+        reinterpret_cast<const S*>(K(it, P.k_Op)), reinterpret_cast<const S*>(K(it, P.k_Om)), P.ldO, P.o, P.v, b.a0,
+        b.b0, b.nb, b.diag, b.npairs, P.minus, it.r->omega, it.r->sy->tbar2,
+        do_E ? X.epart + static_cast<int64_t>(it.ib) * o2 : nullptr);
+    c.launched();
+  }
+}
+
+// Once per system and call, after its last pair block: D to FP64, E summed.
+template <typename T>
+static void finish_system(const SysRun& R, bool do_res, bool do_den, bool do_E, Ctx& c) {
+  const Plan& P = R.P;
+  const Ptrs<T> X(R);
+  const int64_t vv = static_cast<int64_t>(P.v) * P.v;
   if (do_den && Path<T>::mixed) {
-    k_ff_to_f64<<<4096, 256, 0, st>>>(reinterpret_cast<const float2*>(Dacc), D, static_cast<int64_t>(nj) * vv);
+    k_ff_to_f64<<<4096, 256, 0, c.st>>>(reinterpret_cast<const float2*>(X.Dacc), R.D, static_cast<int64_t>(P.nj) * vv);
     c.launched();
   }
   if (do_E && do_res) {
-    k_sum_final<<<1, 1024, 0, st>>>(epart, static_cast<int64_t>(P.pbs.size()) * o2, E);
+    k_sum_final<<<1, 1024, 0, c.st>>>(X.epart, static_cast<int64_t>(P.pbs.size()) * P.o * P.o, R.E);
     c.launched();
   }
+}
+
+// Counted flops of one pair block (g-build, ladder, Gamma, D): the scheduling weight.
+static double block_weight(const Plan& P, const PBlock& b) {
+  const double p = static_cast<double>(b.npairs), v2 = static_cast<double>(P.v) * P.v;
+  const double lad = 2.0 * p * (static_cast<double>(P.Pvp) * P.Pop + static_cast<double>(P.Pvm) * P.Pom);
+  const double rows = b.diag ? static_cast<double>(b.na) * b.na : 2.0 * b.na * b.nb;
+  return 2.0 * p * v2 * P.nj + 2.0 * lad + 2.0 * P.nj * v2 * rows;
+}
+
+// All systems of a call.  Back to back: each system's pair blocks in order
+// through one slot.  Batched: every system prepared first, then waves that
+// take the next pair block of each of the (up to kBatchSlots) systems with
+// the most work left, so each grouped launch carries the tiles of many
+// systems.  Either way a system's pair blocks run in their own order, so its
+// D accumulates in the same order and the results are the same bits.
+template <typename T>
+static void run_all(std::vector<SysRun>& R, const std::vector<Slot>& slots, size_t piece_bytes, bool batched,
+                    bool do_res, bool do_den, bool do_E, Ctx& c) {
+  // The D contraction reads the padding columns inside the Gamma slabs (virtual indices v .. vp-1 of
+  // each row block) against zeros of L, which is only harmless if those columns hold finite values:
+  // the operand-piece part of every slot starts zeroed, and only piece values (finite) are ever
+  // written there, whichever system of the call uses the slot.  (The float-float scratch lives in
+  // the other part of the slot, so its bytes are never read as pieces.)
+  for (const Slot& sl : slots) c.cuda(cudaMemsetAsync(sl.pieces, 0, piece_bytes, c.st));
+  if (!batched) {
+    for (SysRun& r : R) {
+      if (c.err) return;
+      prep_system<T>(r, do_res, do_den, c);
+      if (r.subset.empty()) {
+        for (size_t ib = 0; ib < r.P.pbs.size() && !c.err; ++ib)
+          run_wave<T>({Item{&r, ib, slots[0]}}, do_res, do_den, do_E, c);
+      } else {
+        for (size_t k = 0; k < r.subset.size() && !c.err; ++k)
+          run_wave<T>({Item{&r, r.subset[k], slots[0]}}, do_res, do_den, do_E, c);
+      }
+      if (!c.err) finish_system<T>(r, do_res, do_den, do_E, c);
+    }
+    return;
+  }
+  for (SysRun& r : R) {
+    prep_system<T>(r, do_res, do_den, c);
+    r.next = 0;
+    r.left = 0.0;
+    for (const PBlock& b : r.P.pbs) r.left += block_weight(r.P, b);
+  }
+  std::vector<SysRun*> order;
+  while (!c.err) {
+    order.clear();
+    for (SysRun& r : R)
+      if (r.next < r.P.pbs.size()) order.push_back(&r);
+    if (order.empty()) break;
+    std::stable_sort(order.begin(), order.end(), [](const SysRun* a, const SysRun* b) { return a->left > b->left; });
+    if (order.size() > slots.size()) order.resize(slots.size());
+    std::vector<Item> items;
+    for (size_t k = 0; k < order.size(); ++k) {
+      SysRun* r = order[k];
+      items.push_back(Item{r, r->next, slots[k]});
+      r->left -= block_weight(r->P, r->P.pbs[r->next]);
+      ++r->next;
+    }
+    run_wave<T>(items, do_res, do_den, do_E, c);
+  }
+  if (!c.err)
+    for (SysRun& r : R) finish_system<T>(r, do_res, do_den, do_E, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -1074,20 +1297,30 @@ static int validate(const cc_ladder_system* sys, int n_sys, bool need_tbar) {
   return CC_OK;
 }
 
+// Workspace bytes.  Back to back (which without CC_WS_BATCH): the header, one
+// system region and one scratch slot, each the largest over the systems.
+// Batched (CC_WS_BATCH): the header, every system's own region, and
+// min(n_sys, kBatchSlots) slots.  0 on invalid input.
 static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int which) {
-  size_t need = 0;
+  size_t sys_max = 0, sys_sum = 0, pcs_max = 0, scr_max = 0;
   for (int i = 0; i < n_sys; ++i) {
     Plan P;
     if (!make_plan(sys[i], prec, which, P)) return 0;
-    need = std::max(need, P.total);
+    sys_max = std::max(sys_max, P.sys_bytes);
+    sys_sum += P.sys_bytes;
+    pcs_max = std::max(pcs_max, P.piece_bytes);
+    scr_max = std::max(scr_max, P.scratch_bytes);
   }
-  return need;
+  const size_t slot_max = pcs_max + scr_max;
+  if (which & CC_WS_BATCH)
+    return kStatusBytes + sys_sum + static_cast<size_t>(std::min(n_sys, kBatchSlots)) * slot_max;
+  return kStatusBytes + sys_max + slot_max;
 }
 
 static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* D, double* E,
                int prec, int which, bool res, bool den, bool want_E, void* ws, size_t ws_bytes, void* stream,
                bool adjoint = false, const double* const* es_r2 = nullptr, const double* es_r0 = nullptr,
-               bool clear_status = true) {
+               bool clear_status = true, const std::vector<size_t>* subset = nullptr) {
   if (prec != CC_PREC_FP64 && prec != CC_PREC_MIXED && prec != CC_PREC_FP16X2) return CC_ERR_ARG;
   int rc = validate(sys, n_sys, den || want_E || adjoint);
   if (rc) return rc;
@@ -1102,28 +1335,51 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
   const size_t need = ws_need(sys, n_sys, prec, which);
   if (!need) return CC_ERR_ARG;
   if (ws_bytes < need) return CC_ERR_WORKSPACE;
+  const bool batched = n_sys > 1 && !subset && ws_bytes >= ws_need(sys, n_sys, prec, which | CC_WS_BATCH);
   Ctx c;
   c.st = static_cast<cudaStream_t>(stream);
   c.status = reinterpret_cast<Status*>(ws);
+  c.queue = reinterpret_cast<int*>(static_cast<char*>(ws) + kQueueOffset);
   c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
   c.adjoint = adjoint;
   // every call starts from a clear status word; cc_ladder_status() reads it
   if (clear_status) c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), c.st));
-  for (int i = 0; i < n_sys && !c.err; ++i) {
-    Plan P;
-    make_plan(sys[i], prec, which, P);
-    double* om = (res && omega) ? omega[i] : nullptr;
-    double* Dd = den ? D[i] : nullptr;
-    double* Ei = want_E ? E + i : nullptr;
-    c.r2 = es_r2 ? es_r2[i] : nullptr;
-    c.r0 = es_r0 ? es_r0[i] : 1.0;
-    if (prec == CC_PREC_MIXED)
-      run_system<__nv_bfloat16>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
-    else if (prec == CC_PREC_FP16X2)
-      run_system<__half>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
-    else
-      run_system<double>(sys[i], P, static_cast<char*>(ws), om, Dd, Ei, res, den, want_E, c);
+  std::vector<SysRun> R(n_sys);
+  char* w = static_cast<char*>(ws);
+  size_t cur = kStatusBytes, sys_max = 0, pcs_max = 0, scr_max = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    SysRun& r = R[i];
+    r.sy = &sys[i];
+    make_plan(sys[i], prec, which, r.P);
+    r.omega = (res && omega) ? omega[i] : nullptr;
+    r.D = den ? D[i] : nullptr;
+    r.E = want_E ? E + i : nullptr;
+    r.r2 = es_r2 ? es_r2[i] : nullptr;
+    r.r0 = es_r0 ? es_r0[i] : 1.0;
+    if (subset) {
+      for (size_t ib : *subset)
+        if (ib >= r.P.pbs.size()) return CC_ERR_ARG;
+      r.subset = *subset;
+    }
+    r.base = w + (batched ? cur : kStatusBytes);
+    cur += r.P.sys_bytes;
+    sys_max = std::max(sys_max, r.P.sys_bytes);
+    pcs_max = std::max(pcs_max, r.P.piece_bytes);
+    scr_max = std::max(scr_max, r.P.scratch_bytes);
   }
+  const size_t slot_bytes = pcs_max + scr_max;
+  std::vector<Slot> slots;
+  char* first = batched ? w + cur : w + kStatusBytes + sys_max;
+  for (int k = 0; k < (batched ? std::min(n_sys, kBatchSlots) : 1); ++k) {
+    char* sl = first + static_cast<size_t>(k) * slot_bytes;
+    slots.push_back(Slot{sl, sl + pcs_max});
+  }
+  if (prec == CC_PREC_MIXED)
+    run_all<__nv_bfloat16>(R, slots, pcs_max, batched, res, den, want_E, c);
+  else if (prec == CC_PREC_FP16X2)
+    run_all<__half>(R, slots, pcs_max, batched, res, den, want_E, c);
+  else
+    run_all<double>(R, slots, pcs_max, batched, res, den, want_E, c);
   return c.err;
 }
 
@@ -1153,6 +1409,7 @@ static int run_driver(int o, int v, int nj, const double* L_ov, double* g, const
   Ctx c;
   c.st = st;
   c.status = reinterpret_cast<Status*>(ws);
+  c.queue = reinterpret_cast<int*>(static_cast<char*>(ws) + kQueueOffset);
   c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
   c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
   T* LT = at<T>(ws, d.o_LT);
@@ -1208,6 +1465,7 @@ static int run_ov3(int o, int v, int nj, const double* L_vv, const double* L_ov,
   Ctx c;
   c.st = st;
   c.status = reinterpret_cast<Status*>(ws);
+  c.queue = reinterpret_cast<int*>(static_cast<char*>(ws) + kQueueOffset);
   c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
   c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
   T* P = at<T>(ws, d.o_P);
@@ -1251,6 +1509,7 @@ static int run_ov3_es_abci(int o, int v, int nj, const double* L_vv, const doubl
   Ctx c;
   c.st = st;
   c.status = reinterpret_cast<Status*>(ws);
+  c.queue = reinterpret_cast<int*>(static_cast<char*>(ws) + kQueueOffset);
   c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
   c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
   T* P = at<T>(ws, d.o_P);
@@ -1280,6 +1539,212 @@ static int run_ov3_es_abci(int o, int v, int nj, const double* L_vv, const doubl
   return c.err;
 }
 
+// ---------------------------------------------------------------------------
+// excited-state OV^3: the d_abic block (App. A), eight terms
+// ---------------------------------------------------------------------------
+// d^es_abic = L^a_m t~^cb_im R0 + L^a_m (2 R~^bc_mi - R~^cb_mi) + 2 X_ab R^c_i
+//           - (V_akbi + Y_akbi) R^c_k + L^ad_mk t~^bc_mi R^d_k - L^ad_mn t^bc_mn R^d_i
+//           + Y~_akci R^b_k - X_ac R^b_i
+// contributes W_ab^K = sum_ic d_abic L^K_ic and W_ic^K = sum_ab d_abic L^K_ab
+// (L^K in place of Z^K), built term by term through three-index (and O^2V^2)
+// intermediates, never the OV^3 array.  The large contractions run on the
+// path's contraction engine (operands packed from strided views of the
+// FP64 inputs); the thin ones (one index of length o or 1) as batched FP64
+// products.
+struct Ov3EsPlan {
+  int64_t o, v, nj, ov, vv, oo;
+  size_t o_A, o_B, o_out;
+  size_t o_YP, o_O1, o_X, o_PK, o_QK, o_PKik, o_VY, o_KK, o_Wam, o_Bt, o_Kt, o_Yt, o_QT, o_P2, o_Op1;
+  size_t total;
+};
+
+static Ov3EsPlan ov3es_plan(int o_, int v_, int nj_, int prec) {
+  Ov3EsPlan d;
+  const int64_t o = o_, v = v_, nj = nj_, ov = o * v, vv = v * v, oo = o * o;
+  d.o = o; d.v = v; d.nj = nj; d.ov = ov; d.vv = vv; d.oo = oo;
+  auto R = [](int64_t x) { return rup(x, 64); };
+  // the largest operands (rows x padded K) and outputs (N x M) of the contraction sequence below
+  const int64_t a_max = std::max({ov * R(ov), v * R(oo * v), vv * R(oo), oo * R(vv), v * R(oo), vv * R(v), v * R(vv)});
+  const int64_t b_max = std::max({nj * R(ov), v * R(oo * v), ov * R(ov), nj * R(oo), nj * R(vv), vv * R(oo), nj * R(v)});
+  const int64_t out_max = std::max({nj * ov, vv, ov * ov, nj * vv, nj * oo, vv * v, nj * v});
+  const int op = prec == CC_PREC_FP64 ? CC_PREC_FP64 : CC_PREC_MIXED;
+  size_t cur = kStatusBytes;
+  auto take = [&](size_t bytes) {
+    const size_t at = cur;
+    cur += rup(static_cast<int64_t>(bytes), 256);
+    return at;
+  };
+  d.o_A = take(mat_bytes(op, a_max, 1));
+  d.o_B = take(mat_bytes(op, b_max, 1));
+  d.o_out = take(static_cast<size_t>(out_max) * 8);
+  d.o_YP = take(nj * ov * 8);
+  d.o_O1 = take(nj * ov * 8);
+  d.o_X = take(vv * 8);
+  d.o_PK = take(nj * 8);
+  d.o_QK = take(nj * 8);
+  d.o_PKik = take(nj * oo * 8);
+  d.o_VY = take(ov * ov * 8);
+  d.o_KK = take(nj * oo * 8);
+  d.o_Wam = take(ov * 8);
+  d.o_Bt = take(oo * ov * 8);
+  d.o_Kt = take(v * vv * 8);
+  d.o_Yt = take(ov * ov * 8);
+  d.o_QT = take(nj * ov * 8);
+  d.o_P2 = take(nj * ov * 8);
+  d.o_Op1 = take(nj * ov * 8);
+  d.total = cur;
+  return d;
+}
+
+template <typename T>
+struct EsContract {
+  using S = typename Path<T>::S;
+  Ctx& c;
+  char* ws;
+  const Ov3EsPlan& d;
+  static unsigned grid(int64_t n) { return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(4096, (n + 255) / 256))); }
+  // out[n][m] = sum_k A[m][k] B[n][k], A rows m = (r1, r2) of the views a1 + a2, B rows n likewise,
+  // k = (k1, k2); returns the contraction output (row pitch M)
+  const S* run(View a1, View a2, int64_t MR1, int64_t MR2, View b1, View b2, int64_t NR1, int64_t NR2, int64_t K1,
+               int64_t K2) {
+    const int64_t M = MR1 * MR2, N = NR1 * NR2, ld = rup(K1 * K2, 64);
+    T* A = at<T>(ws, d.o_A);
+    T* B = at<T>(ws, d.o_B);
+    S* out = at<S>(ws, d.o_out);
+    k_pack_view<T><<<grid(M * ld), 256, 0, c.st>>>(a1, a2, MR1, MR2, K1, K2, A, ld, M * ld);
+    k_pack_view<T><<<grid(N * ld), 256, 0, c.st>>>(b1, b2, NR1, NR2, K1, K2, B, ld, N * ld);
+    c.launched(2);
+    const Gm g = {A, ld, M, ld, M * ld, B, ld, N, ld, N * ld, M, N, ld, out, M, false};
+    run_gemms<T>(&g, 1, c);
+    return out;
+  }
+  // dst[n*sdn + m*sdm] (= | +=) alpha * out[n][m]
+  void put(const S* src, int64_t M, int64_t N, double alpha, double* dst, int64_t sdn, int64_t sdm, bool acc) {
+    k_out_view<S><<<grid(M * N), 256, 0, c.st>>>(src, M, M, N, alpha, dst, sdn, sdm, acc ? 1 : 0);
+    c.launched();
+  }
+  void bat(const BatchedF64& g) { c.check(batched_gemm_f64(g, c.st)); }
+};
+
+template <typename T>
+static int run_ov3_es_abic(int o_, int v_, int nj_, const double* L_vv, const double* L_ov, const double* tbar1,
+                           const double* L2, const double* t2, double R0, const double* R1, const double* R2,
+                           double* W_vv, double* W_ov, const Ov3EsPlan& d, char* ws, cudaStream_t st) {
+  Ctx c;
+  c.st = st;
+  c.status = reinterpret_cast<Status*>(ws);
+  c.queue = reinterpret_cast<int*>(ws + kQueueOffset);
+  c.timeout_ns = static_cast<uint64_t>(env_int("CC_TIMEOUT_MS", 4000)) * 1000000ull;
+  c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), st));
+  EsContract<T> E{c, ws, d};
+  using S = typename Path<T>::S;
+  const int o = o_, v = v_, nj = nj_;
+  const int64_t ov = d.ov, vv = d.vv, oo = d.oo, ovv = static_cast<int64_t>(o) * vv;
+  double* YP = at<double>(ws, d.o_YP);
+  double* O1 = at<double>(ws, d.o_O1);
+  double* X = at<double>(ws, d.o_X);
+  double* PK = at<double>(ws, d.o_PK);
+  double* QK = at<double>(ws, d.o_QK);
+  double* PKik = at<double>(ws, d.o_PKik);
+  double* VY = at<double>(ws, d.o_VY);
+  double* KK = at<double>(ws, d.o_KK);
+  double* Wam = at<double>(ws, d.o_Wam);
+  double* Bt = at<double>(ws, d.o_Bt);
+  double* Kt = at<double>(ws, d.o_Kt);
+  double* Yt = at<double>(ws, d.o_Yt);
+  double* QT = at<double>(ws, d.o_QT);
+  double* P2 = at<double>(ws, d.o_P2);
+  double* Op1 = at<double>(ws, d.o_Op1);
+  const View none{nullptr, 0, 0, 0, 0, 0.0};
+  c.cuda(cudaMemsetAsync(W_vv, 0, static_cast<size_t>(nj) * vv * 8, st));
+  c.cuda(cudaMemsetAsync(W_ov, 0, static_cast<size_t>(nj) * ov * 8, st));
+
+  // W_am = L^ad_mk R^d_k  ([m][a], one batched product per k)
+  for (int k = 0; k < o && !c.err; ++k)
+    E.bat({1, v, v, o, R1 + static_cast<int64_t>(k) * v, 0, 1, L2 + static_cast<int64_t>(k) * vv, ovv, 1, v,
+           k ? Wam : nullptr, v, 0, 1, 1.0, Wam, v, 0, 1});
+  // X_ab = L^ad_kl t^bd_kl  (M = a, N = b, K = (kl, d)), then P^K = R^c_i L^K_ic and Q^K = X_ab L^K_ab
+  E.put(E.run({L2, v, 0, vv, 1, 1.0}, none, v, 1, {t2, v, 0, vv, 1, 1.0}, none, v, 1, oo, v), v, v, 1.0, X, 1, v,
+        false);
+  E.bat({1, 1, static_cast<int>(ov), nj, R1, 0, 1, L_ov, ov, 1, 0, nullptr, 0, 0, 0, 1.0, PK, 1, 0, 0});
+  E.bat({1, 1, static_cast<int>(vv), nj, X, 0, 1, L_vv, vv, 1, 0, nullptr, 0, 0, 0, 1.0, QK, 1, 0, 0});
+
+  // terms 1, 2 and 5: left factor (L^a_m, then W_am) times a pair matrix P[(i,c)][(m,b)] (symmetric):
+  // W_ab += left[m][a] sum_ic P^cb_im L^K_ic, W_ic += sum_mb P^cb_im (sum_a left[m][a] L^K_ab)
+  const int64_t Kov = rup(ov, 64);
+  for (int pass = 0; pass < 2 && !c.err; ++pass) {
+    T* A = at<T>(ws, d.o_A);
+    T* B = at<T>(ws, d.o_B);
+    const S* out = at<S>(ws, d.o_out);
+    if (pass == 0)  // R0 t~ + 2 R~^bc_mi - R~^cb_mi = R0 (2 t_im - t_mi)^cb + (5 R_im - 4 R_mi)^cb
+      k_pack_pairmat<T><<<static_cast<unsigned>(ov), 256, 0, st>>>(t2, o, v, 2.0 * R0, -R0, A, Kov, ov * Kov, R2,
+                                                                    5.0, -4.0);
+    else
+      k_pack_pairmat<T><<<static_cast<unsigned>(ov), 256, 0, st>>>(t2, o, v, 2.0, -1.0, A, Kov, ov * Kov);
+    c.launched();
+    const double* left = pass == 0 ? tbar1 : Wam;
+    k_pack_view<T><<<EsContract<T>::grid(nj * Kov), 256, 0, st>>>(View{L_ov, ov, 0, 1, 0, 1.0}, none, nj, 1, ov, 1, B,
+                                                                  Kov, nj * Kov);
+    c.launched();
+    const Gm g1 = {A, Kov, ov, Kov, ov * Kov, B, Kov, nj, Kov, nj * Kov, ov, nj, Kov, const_cast<S*>(out), ov, false};
+    run_gemms<T>(&g1, 1, c);
+    E.put(out, ov, nj, 1.0, YP, ov, 1, false);                                        // YP[K][(m,b)]
+    E.bat({v, v, o, nj, left, 1, v, YP, ov, v, 1, W_vv, vv, v, 1, 1.0, W_vv, vv, v, 1});
+    E.bat({o, v, v, nj, left, v, 1, L_vv, vv, v, 1, nullptr, 0, 0, 0, 1.0, O1, ov, v, 1});
+    k_pack_view<T><<<EsContract<T>::grid(nj * Kov), 256, 0, st>>>(View{O1, ov, 0, 1, 0, 1.0}, none, nj, 1, ov, 1, B,
+                                                                  Kov, nj * Kov);
+    c.launched();
+    const Gm g2 = {A, Kov, ov, Kov, ov * Kov, B, Kov, nj, Kov, nj * Kov, ov, nj, Kov, const_cast<S*>(out), ov, false};
+    run_gemms<T>(&g2, 1, c);
+    E.put(out, ov, nj, 1.0, W_ov, ov, 1, true);
+  }
+
+  // term 3: 2 X_ab R^c_i
+  E.bat({static_cast<int>(vv), 1, 1, nj, X, 1, 0, PK, 1, 0, 0, W_vv, vv, 1, 0, 2.0, W_vv, vv, 1, 0});
+  E.bat({static_cast<int>(ov), 1, 1, nj, R1, 1, 0, QK, 1, 0, 0, W_ov, ov, 1, 0, 2.0, W_ov, ov, 1, 0});
+
+  // term 4: -(V_akbi + Y_akbi) R^c_k, VY[(b,i)][(a,k)] = V + Y (two contractions over (j,c) and (l,d))
+  E.put(E.run({L2, v, vv, ovv, 1, 1.0}, none, v, o, {t2, v, vv, ovv, 1, 1.0}, none, v, o, o, v), ov, ov, 1.0, VY, ov,
+        1, false);
+  E.put(E.run({L2, v, ovv, vv, 1, 1.0}, none, v, o, {t2, v, ovv, vv, 1, 1.0}, none, v, o, o, v), ov, ov, 1.0, VY, ov,
+        1, true);
+  E.bat({o, o, v, nj, R1, v, 1, L_ov, ov, 1, v, nullptr, 0, 0, 0, 1.0, PKik, oo, o, 1});        // PKik[K][k][i]
+  E.put(E.run({VY, o, o * ov, ov, 1, 1.0}, none, v, v, {PKik, oo, 0, 1, o, 1.0}, none, nj, 1, o, o), vv, nj, -1.0,
+        W_vv, vv, 1, true);
+  E.put(E.run({VY, ov, 1, o, o * ov, 1.0}, none, o, o, {L_vv, vv, 0, v, 1, 1.0}, none, nj, 1, v, v), oo, nj, 1.0, KK,
+        oo, 1, false);                                                                   // KK[K][i][k]
+  E.bat({v, o, o, nj, R1, 1, v, KK, oo, 1, o, W_ov, ov, 1, v, -1.0, W_ov, ov, 1, v});
+
+  // term 6: -B_iamn t^bc_mn with B_iamn = L^ad_mn R^d_i, one i at a time (K_i[(b,c)][a] = sum_mn B t)
+  E.bat({o, v, v, static_cast<int>(oo), R1, v, 1, L2, vv, 1, v, nullptr, 0, 0, 0, 1.0, Bt, ov, v, 1});  // Bt[mn][i][a]
+  for (int i = 0; i < o && !c.err; ++i) {
+    E.put(E.run({Bt + static_cast<int64_t>(i) * v, 1, 0, ov, 0, 1.0}, none, v, 1, {t2, v, 1, vv, 0, 1.0}, none, v, v,
+                oo, 1),
+          v, vv, 1.0, Kt, v, 1, false);
+    E.put(E.run({Kt, 1, vv, v, 0, 1.0}, none, v, v, {L_ov + static_cast<int64_t>(i) * v, ov, 0, 1, 0, 1.0}, none, nj,
+                1, v, 1),
+          vv, nj, -1.0, W_vv, vv, 1, true);
+    E.put(E.run({Kt, v, 0, 1, vv, 1.0}, none, v, 1, {L_vv, vv, 0, v, 1, 1.0}, none, nj, 1, v, v), v, nj, -1.0,
+          W_ov + static_cast<int64_t>(i) * v, ov, 1, true);
+  }
+
+  // term 7: Y~_akci R^b_k, Yt[(c,i)][(a,k)] = L^ea_mk t~^ec_mi (t~ = 2 t_mi - t_im)
+  E.put(E.run({L2, 1, vv, ovv, v, 1.0}, none, v, o, {t2, 1, vv, ovv, v, 2.0}, {t2, 1, ovv, vv, v, -1.0}, v, o, o, v),
+        ov, ov, 1.0, Yt, ov, 1, false);
+  E.put(E.run({Yt, o, 1, ov, o * ov, 1.0}, none, v, o, {L_ov, ov, 0, v, 1, 1.0}, none, nj, 1, o, v), ov, nj, 1.0, QT,
+        ov, 1, false);                                                                   // QT[K][a][k]
+  E.bat({v, v, o, nj, R1, 1, v, QT, ov, 1, o, W_vv, vv, 1, v, 1.0, W_vv, vv, 1, v});
+  E.bat({o, v, v, nj, R1, v, 1, L_vv, vv, 1, v, nullptr, 0, 0, 0, 1.0, P2, ov, v, 1});         // P2[K][k][a]
+  E.put(E.run({Yt, ov, o * ov, o, 1, 1.0}, none, o, v, {P2, ov, 0, 1, v, 1.0}, none, nj, 1, v, o), ov, nj, 1.0, W_ov,
+        ov, 1, true);
+
+  // term 8: -X_ac R^b_i
+  E.bat({v, o, v, nj, X, v, 1, L_ov, ov, 1, v, nullptr, 0, 0, 0, 1.0, Op1, ov, o, 1});        // Op1[K][a][i]
+  E.bat({v, v, o, nj, R1, 1, v, Op1, ov, 1, o, W_vv, vv, 1, v, -1.0, W_vv, vv, 1, v});
+  E.bat({v, o, v, nj, X, 1, v, P2, ov, 1, v, W_ov, ov, 1, v, -1.0, W_ov, ov, 1, v});
+  return c.err;
+}
+
 }  // namespace ccl
 
 using namespace ccl;
@@ -1301,6 +1766,35 @@ int cc_ladder_ov3_es_abci(int32_t o, int32_t v, int32_t nj, const double* L_vv, 
   if (p == CC_PREC_FP64)
     return run_ov3_es_abci<double>(o, v, nj, L_vv, L_ov, L2, R1, W_vv, W_vo, d, static_cast<char*>(ws), st);
   return run_ov3_es_abci<__nv_bfloat16>(o, v, nj, L_vv, L_ov, L2, R1, W_vv, W_vo, d, static_cast<char*>(ws), st);
+}
+
+size_t cc_ladder_ov3_es_abic_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p) {
+  if (o < 1 || v < 1 || nj < 1 || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2)) return 0;
+  return ov3es_plan(o, v, nj, p).total;
+}
+
+int cc_ladder_ov3_es_abic(int32_t o, int32_t v, int32_t nj, const double* L_vv, const double* L_ov,
+                          const double* tbar1, const double* L2, const double* t2, double R0, const double* R1,
+                          const double* R2, double* W_vv, double* W_ov, cc_precision p, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (o < 1 || v < 1 || nj < 1 || !L_vv || !L_ov || !tbar1 || !L2 || !t2 || !R1 || !R2 || !W_vv || !W_ov)
+    return CC_ERR_ARG;
+  for (const void* q : {static_cast<const void*>(L_vv), static_cast<const void*>(L_ov),
+                        static_cast<const void*>(tbar1), static_cast<const void*>(L2), static_cast<const void*>(t2),
+                        static_cast<const void*>(R1), static_cast<const void*>(R2), static_cast<const void*>(W_vv),
+                        static_cast<const void*>(W_ov)})
+    if (!aligned8(q)) return CC_ERR_ARG;
+  if (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) return CC_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return CC_ERR_ARG;
+  if (const int rc = check_device()) return rc;
+  const Ov3EsPlan d = ov3es_plan(o, v, nj, p);
+  if (ws_bytes < d.total) return CC_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p == CC_PREC_FP64)
+    return run_ov3_es_abic<double>(o, v, nj, L_vv, L_ov, tbar1, L2, t2, R0, R1, R2, W_vv, W_ov, d,
+                                   static_cast<char*>(ws), st);
+  return run_ov3_es_abic<__nv_bfloat16>(o, v, nj, L_vv, L_ov, tbar1, L2, t2, R0, R1, R2, W_vv, W_ov, d,
+                                        static_cast<char*>(ws), st);
 }
 
 size_t cc_ladder_ov3_workspace_size(int32_t o, int32_t v, int32_t nj, cc_precision p) {
@@ -1392,7 +1886,7 @@ int cc_ladder_iterate(const cc_ladder_system* sys, const double* g_drv, int n_it
 
 size_t cc_ladder_workspace_size(const cc_ladder_system* sys, int n_sys, cc_precision p, int which) {
   if (validate(sys, n_sys, false) || (p != CC_PREC_FP64 && p != CC_PREC_MIXED && p != CC_PREC_FP16X2) ||
-      !(which & CC_WS_STEP))
+      !(which & CC_WS_STEP) || (which & ~(CC_WS_STEP | CC_WS_BATCH)))
     return 0;
   return ws_need(sys, n_sys, p, which);
 }
@@ -1464,6 +1958,35 @@ int cc_ladder_step(const cc_ladder_system* sys, int n_sys, double* const* omega,
   return run(sys, n_sys, omega, D, E, p, CC_WS_STEP, true, true, true, ws, ws_bytes, stream);
 }
 
+int cc_ladder_pair_blocks(const cc_ladder_system* sys, int32_t* count, int32_t* edge) {
+  if (validate(sys, 1, false) || !count) return CC_ERR_ARG;
+  Plan P;
+  if (!make_plan(*sys, CC_PREC_FP64, CC_WS_STEP, P)) return CC_ERR_ARG;
+  *count = static_cast<int32_t>(P.pbs.size());
+  if (edge) *edge = P.s;
+  return CC_OK;
+}
+
+int cc_ladder_step_blocks(const cc_ladder_system* sys, const int32_t* blocks, int n_blocks, double* omega,
+                          double* D_part, double* E_part, cc_precision p, void* ws, size_t ws_bytes, void* stream) {
+  if (!sys || !blocks || n_blocks < 1 || !omega || !D_part || !E_part) return CC_ERR_ARG;
+  if (validate(sys, 1, true)) return CC_ERR_ARG;
+  Plan P;
+  if (!make_plan(*sys, CC_PREC_FP64, CC_WS_STEP, P)) return CC_ERR_ARG;
+  std::vector<size_t> subset;
+  std::vector<char> seen(P.pbs.size(), 0);
+  for (int k = 0; k < n_blocks; ++k) {
+    const int32_t b = blocks[k];
+    if (b < 0 || static_cast<size_t>(b) >= P.pbs.size() || seen[b]) return CC_ERR_ARG;  // out of range or repeated
+    seen[b] = 1;
+    subset.push_back(static_cast<size_t>(b));
+  }
+  double* om[1] = {omega};
+  double* Dp[1] = {D_part};
+  return run(sys, 1, om, Dp, E_part, p, CC_WS_STEP, true, true, true, ws, ws_bytes, stream, false, nullptr, nullptr,
+             true, &subset);
+}
+
 int cc_ladder_update(const cc_ladder_system* sys, int n_sys, double* const* omega, double* const* t2_out,
                      void* stream) {
   int rc = validate(sys, n_sys, false);
@@ -1480,6 +2003,20 @@ int cc_ladder_update(const cc_ladder_system* sys, int n_sys, double* const* omeg
       note_cuda(e);
       return CC_ERR_CUDA;
     }
+  }
+  return CC_OK;
+}
+
+int cc_ladder_scale_by(double* x, int64_t n, double factor, const double* g, void* stream) {
+  if (!x || n < 1 || !aligned8(x) || !aligned8(g)) return CC_ERR_ARG;
+  if (const int rc = check_device()) return rc;
+  const int64_t blocks = std::min<int64_t>(4096, (n + 255) / 256);
+  k_scale_by<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, factor, g);
+  count_launch();
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return CC_ERR_CUDA;
   }
   return CC_OK;
 }

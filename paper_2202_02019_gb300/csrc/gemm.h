@@ -6,11 +6,13 @@
 // The output is written transposed (M contiguous) so that a warp's lanes,
 // which hold consecutive rows m of the accumulator, store coalesced.
 //
-// Mixed paths (gemm_mixed): split operands (3 BF16 or 2 scaled FP16 pieces), one CTA per 128 x 128
-// output tile over the whole K, float-float output (float2 hi/lo) either
-// stored (OUT_FF_STORE) or added to what is there (OUT_FF_ACCUM, a plain
-// read-modify-write: tiles are owned by one CTA).  Up to two problems of
-// the same kind run in one launch (grid z selects the problem).
+// Mixed paths (gemm_mixed): split operands (3 BF16 or 2 scaled FP16 pieces), 128 x 128 output
+// tiles each computed by one CTA over the whole K, float-float output (float2
+// hi/lo) either stored (OUT_FF_STORE) or added to what is there (OUT_FF_ACCUM,
+// a plain read-modify-write: tiles are owned by one CTA).  Up to
+// GEMM_MAX_PROBLEMS independent problems of the same piece scheme run in one
+// persistent launch whose CTAs pull tiles from a device queue; problems of one
+// launch must not write overlapping outputs.
 // FP64 path (gemm_f64): FP64 operands and output; K may be split into
 // chunks that are added with FP64 atomics (OUT_F64_ATOMIC, caller zeroes).
 #pragma once
@@ -22,6 +24,8 @@
 namespace ccl {
 
 enum OutMode { OUT_F64_STORE = 0, OUT_F64_ATOMIC = 1, OUT_FF_STORE = 2, OUT_FF_ACCUM = 3 };
+
+constexpr int GEMM_MAX_PROBLEMS = 64;  // problems per mixed launch (kernel parameter space)
 
 struct GemmOp {
   // A: rows a_rows (rows past it read as zero), a_cols valid columns
@@ -43,10 +47,12 @@ struct GemmOp {
                                    // `tri` rows past every column block (only the upper block triangle of a
                                    // symmetric product is read later); the skipped output is left unwritten
   Status* status = nullptr;
+  int* queue = nullptr;         // mixed path: device int, the launch's tile counter (zeroed by the launch)
   uint64_t timeout_ns = 2000000000ull;
 };
 
-// Returns 0 or a negative CC_ERR_* code.
+// Returns 0 or a negative CC_ERR_* code.  ops[0].status and ops[0].queue
+// serve the whole mixed launch.
 int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream);
 int gemm_f64(const GemmOp& op, cudaStream_t stream);
 

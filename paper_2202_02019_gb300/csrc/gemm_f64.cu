@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(256) cc_gemm_f64_dmma(const double* __restrict
 
 int gemm_f64(const GemmOp& op, cudaStream_t stream) {
   if (op.M <= 0 || op.N <= 0 || op.K <= 0) return 0;
+  if (!op.A || !op.B || !op.out) return -1;  // never launch on a missing operand or output
   if (op.mode != OUT_F64_STORE && op.mode != OUT_F64_ATOMIC) return -1;
   if (op.M > (int64_t)FBM * 65535 || op.K > 2147483647LL) return -1;
   const int64_t kc = op.kchunk ? std::min<int64_t>(op.kchunk, op.K) : op.K;

@@ -34,15 +34,31 @@
 // ran 10-25% slower.  One CTA owns a 128 x 128 output tile over the whole K
 // and writes the float-float result hi + lo (or adds it to the value there).
 //
-// CTA = 18 warps: warp 0 issues TMA loads (one elected lane), warp 1 owns
-// TMEM and issues tcgen05.mma (one elected lane), warps 2-17 drain (warp w
-// reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  Tile
-// 128 x 128 x 64 with a 192 KB smem ring (BF16: 2 stages of 3 A + 3 B
-// pieces; FP16: 3 stages of 2 + 2), 128-byte swizzle (128-byte TMA rows move
-// operands ~1.2x faster than 64-byte ones).  Every CTA loads its own A and B
-// tiles (one 3-D box of all pieces each).  TMEM columns:
-// H0 [0,128), H1 [128,256), L [256,384), LO [384,512).
-// Every wait is bounded (globaltimer) and latches CC_ERR_TIMEOUT.
+// Persistent, grouped launch.  One launch takes a list of up to MAXP
+// independent problems (the +- pair of one contraction, both D slabs, or the
+// same contraction of many systems of a batch); their 128 x 128 output tiles
+// form one flattened list, problems ordered by K (longest first).  The grid
+// holds at most one CTA per SM, and each CTA pulls tiles from a device work
+// queue (an atomic counter in the workspace header) until the list is empty.
+// Barriers, TMEM and the smem ring live across tiles, so the TMA warp loads
+// the next tile while the MMA warp finishes the current one, and the MMA warp
+// starts the next tile's windows while the drain warps write the previous
+// tile's result.  Every tile is computed by one CTA over its whole K in the
+// same arithmetic order whatever CTA takes it: results are bit-for-bit
+// independent of the scheduling and of the grouping.
+//
+// CTA = 18 warps: warp 0 pulls tiles and issues TMA loads (one elected lane),
+// warp 1 owns TMEM and issues tcgen05.mma (one elected lane), warps 2-17 drain
+// (warp w reads TMEM lane quarter w%4 and the 32-column slice (w-2)/4).  The
+// TMA warp hands each tile's (problem, m0, n0) to the others through a
+// two-entry shared-memory ring.  Tile 128 x 128 x 64 with a 192 KB smem ring
+// (BF16: 2 stages of 3 A + 3 B pieces; FP16: 3 stages of 2 + 2), 128-byte
+// swizzle (128-byte TMA rows move operands ~1.2x faster than 64-byte ones).
+// Every CTA loads its own A and B tiles (one 3-D box of all pieces each).
+// TMEM columns: H0 [0,128), H1 [128,256), L [256,384), LO [384,512).
+// Every wait is bounded (globaltimer) and latches CC_ERR_TIMEOUT; on the way
+// out the TMA warp waits (bounded) for its own copies in flight and the MMA
+// warp for its own MMAs before TMEM is released.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -51,6 +67,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <numeric>
+#include <vector>
 
 #include "gemm.h"
 
@@ -61,13 +79,15 @@ constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int RASTER_GROUP = 8;           // m-tiles per raster group (L2 reuse of B panels)
 constexpr int A_PIECE = BM * BK * 2;      // 16384 B (one 16-bit piece of a 128 x 64 tile)
 constexpr int B_PIECE = BN * BK * 2;      // 16384 B
-constexpr int SMEM_BYTES = 196608 + 1024 + 256;  // stages * stage bytes is 192 KB for both schemes
+constexpr int SMEM_BYTES = 196608 + 1024 + 512;  // stages * stage bytes is 192 KB for both schemes
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int FOLD = 32;                  // H windows summed in FP32 before the error-free fold
 constexpr uint32_t COL_H0 = 0, COL_H1 = 128, COL_L = 256, COL_LO = 384;
 constexpr int NDRAIN = 16;                // draining warps (4 per TMEM lane quarter)
 constexpr int NTHREADS = (2 + NDRAIN) * 32;
 constexpr int DCOLS = BN / (NDRAIN / 4);  // accumulator columns per drain thread
+constexpr int TRING = 2;                  // tile hand-off ring entries
+constexpr int MAXP = GEMM_MAX_PROBLEMS;
 
 // Piece schemes.  NP = 3: BF16 pieces, six products, the leading one last.
 // NP = 2: FP16 pieces of power-of-two scaled operands, three products.
@@ -111,15 +131,52 @@ struct Prob {
   long long ldo;
   int M, N, K, mode;
   int tri;             // > 0: skip output tiles with every row block above every column block
+  int mt, nt;          // m-tiles, n-tiles
+  int tile0;           // first entry of this problem in the flattened tile list
 };
 struct Probs {
-  Prob p[2];
+  Prob p[MAXP];
+  int nprob;
+  int total;   // tiles in the flattened list
   int win_kb;  // k-blocks per H window
   int lwin;    // H windows per L segment
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that ignores the abort flag (used on the way out, for work this
+// thread itself put in flight).
+__device__ __forceinline__ bool mbar_wait_own(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > timeout_ns) return false;
+  return true;
+}
+
+// Flattened tile t -> (problem, m0, n0); false for a tile the problem skips.
+__device__ __forceinline__ bool decode_tile(const Probs& P, int t, int& pi, int& m0, int& n0) {
+  int p = 0;
+  while (p + 1 < P.nprob && P.p[p + 1].tile0 <= t) ++p;
+  const Prob& pr = P.p[p];
+  // grouped raster: consecutive tiles sweep the n-tiles of RASTER_GROUP m-tiles
+  const int lin = t - pr.tile0;
+  const int grp = lin / (RASTER_GROUP * pr.nt);
+  const int gm0 = grp * RASTER_GROUP;
+  const int gsz = min(RASTER_GROUP, pr.mt - gm0);
+  const int in_grp = lin - grp * RASTER_GROUP * pr.nt;
+  pi = p;
+  m0 = (gm0 + in_grp % gsz) * BM;
+  n0 = (in_grp / gsz) * BN;
+  if (pr.tri > 0) {
+    // rows and columns come in blocks of pr.tri (a symmetric product's pair index): a tile whose
+    // smallest row block lies past its largest column block computes nothing anybody reads
+    const int n_end = min(pr.N, n0 + BN);
+    if (m0 / pr.tri > (n_end - 1) / pr.tri) return false;
+  }
+  return true;
 }
 
 // error-free FP32 accumulation: hi + lo += x
@@ -176,28 +233,12 @@ __device__ __forceinline__ void fold_cols(uint32_t lo_addr, float (&acc)[DCOLS],
 
 template <int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    cc_gemm_split3_tc(const __grid_constant__ Probs P, Status* st, unsigned long long timeout_ns) {
+    cc_gemm_split3_tc(const __grid_constant__ Probs P, int* __restrict__ queue, Status* st,
+                      unsigned long long timeout_ns) {
   using SC = Scheme<NP>;
   constexpr int STAGES = SC::STAGES;
   constexpr int A_STAGE = NP * A_PIECE, B_STAGE = NP * B_PIECE, STAGE = A_STAGE + B_STAGE;
-  const Prob& pr = P.p[blockIdx.z];
   const int WIN_KB = P.win_kb, LWIN = P.lwin;
-  // grouped raster: consecutive CTAs sweep the n-tiles of RASTER_GROUP m-tiles
-  const int mt_n = (pr.M + BM - 1) / BM, nt_n = (pr.N + BN - 1) / BN;
-  const int lin = blockIdx.x;
-  if (lin >= mt_n * nt_n) return;  // CTA outside this problem
-  const int grp = lin / (RASTER_GROUP * nt_n);
-  const int gm0 = grp * RASTER_GROUP;
-  const int gsz = min(RASTER_GROUP, mt_n - gm0);
-  const int in_grp = lin - grp * RASTER_GROUP * nt_n;
-  const int m0 = (gm0 + in_grp % gsz) * BM;
-  const int n0 = (in_grp / gsz) * BN;
-  if (pr.tri > 0) {
-    // rows and columns come in blocks of pr.tri (a symmetric product's pair index): a tile whose
-    // smallest row block lies past its largest column block computes nothing anybody reads
-    const int n_end = min(pr.N, n0 + BN);
-    if (m0 / pr.tri > (n_end - 1) / pr.tri) return;
-  }
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -207,12 +248,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* hempty = hfull + 2;       // [2]
   uint64_t* lfull = hempty + 2;       // [1]
   uint64_t* lempty = lfull + 1;       // [1]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(lempty + 1);
+  uint64_t* tfull = lempty + 1;       // [TRING]
+  uint64_t* tempty = tfull + TRING;   // [TRING]
+  uint64_t* mdone = tempty + TRING;   // [1]
+  int4* ring = reinterpret_cast<int4*>(mdone + 2);  // [TRING] (16-byte aligned)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ring + TRING);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkb = pr.K / BK;
-  const int nwin = (nkb + WIN_KB - 1) / WIN_KB;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -225,10 +268,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     mbar_init(lfull, 1);
     mbar_init(lempty, NDRAIN);
+    for (int r = 0; r < TRING; ++r) {
+      mbar_init(&tfull[r], 1);
+      mbar_init(&tempty[r], 1 + NDRAIN);  // the MMA lane and every drain warp
+    }
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     fence_mbar_init();
-    tma_prefetch(&pr.ta);
-    tma_prefetch(&pr.tb);
   }
   if (warp == 1) {
     tmem_alloc(tslot, TMEM_COLS);
@@ -241,68 +287,121 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort_flag, timeout_ns)) {
-          latch_error(st, kErrTimeout, 101);
+      // producer: pull tiles from the queue, hand them on, load their operands
+      long long g = 0;  // k-blocks issued so far (stage ring position)
+      int tc = 0;       // tiles handed on so far (tile ring position)
+      bool ok = true;
+      while (ok) {
+        int pi = -1, m0 = 0, n0 = 0;
+        for (;;) {
+          const int t = atomicAdd(queue, 1);
+          if (t >= P.total) break;
+          if (decode_tile(P, t, pi, m0, n0)) break;
+          pi = -1;
+        }
+        const int slot = tc % TRING;
+        if (!mbar_wait_bounded(&tempty[slot], ((tc / TRING) & 1) ^ 1, abort_flag, timeout_ns)) {
+          latch_error(st, kErrTimeout, 106);
           break;
         }
-        uint8_t* sa = smem + s * STAGE;
-        mbar_expect_tx(&full[s], STAGE);  // every piece of the A and B tiles
-        tma_load_3d(&pr.ta, &full[s], sa, kb * BK, m0, 0);
-        tma_load_3d(&pr.tb, &full[s], sa + A_STAGE, kb * BK, n0, 0);
+        ring[slot] = make_int4(pi, m0, n0, 0);
+        mbar_arrive(&tfull[slot]);
+        ++tc;
+        if (pi < 0) break;
+        const Prob& pr = P.p[pi];
+        const int nkb = pr.K / BK;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          const uint32_t ph = static_cast<uint32_t>((g / STAGES) & 1);
+          if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort_flag, timeout_ns)) {
+            latch_error(st, kErrTimeout, 101);
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + s * STAGE;
+          mbar_expect_tx(&full[s], STAGE);  // every piece of the A and B tiles
+          tma_load_3d(&pr.ta, &full[s], sa, kb * BK, m0, 0);
+          tma_load_3d(&pr.tb, &full[s], sa + A_STAGE, kb * BK, n0, 0);
+        }
       }
+      // our own copies still in flight (only after an abort) land before the CTA leaves
+      for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+        mbar_wait_own(&full[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1), timeout_ns);
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      long long g = 0;  // k-blocks consumed
+      int gw = 0;       // H windows issued (H buffer = gw & 1)
+      int gl = 0;       // L segments issued
+      int tc = 0;
       bool ok = true;
-      for (int w = 0; w < nwin && ok; ++w) {
-        const int hb = w & 1;
-        const uint32_t hcol = hb ? COL_H1 : COL_H0;
-        const bool lseg_start = (w % LWIN) == 0;
-        if (w >= 2 && !mbar_wait_bounded(&hempty[hb], ((w >> 1) - 1) & 1, abort_flag, timeout_ns)) {
-          latch_error(st, kErrTimeout, 104);
+      while (ok) {
+        const int slot = tc % TRING;
+        if (!mbar_wait_bounded(&tfull[slot], (tc / TRING) & 1, abort_flag, timeout_ns)) {
+          latch_error(st, kErrTimeout, 107);
           break;
         }
-        if (w > 0 && lseg_start &&
-            !mbar_wait_bounded(lempty, ((w / LWIN) - 1) & 1, abort_flag, timeout_ns)) {
-          latch_error(st, kErrTimeout, 105);
-          break;
-        }
-        tc_fence_after();
-        const int kb_beg = w * WIN_KB, kb_end = min(nkb, (w + 1) * WIN_KB);
-        for (int kb = kb_beg; kb < kb_end; ++kb) {
-          const int s = kb % STAGES;
-          const uint32_t ph = (kb / STAGES) & 1;
-          if (!mbar_wait_bounded(&full[s], ph, abort_flag, timeout_ns)) {
-            latch_error(st, kErrTimeout, 102);
+        const int4 e = ring[slot];
+        mbar_arrive(&tempty[slot]);
+        ++tc;
+        if (e.x < 0) break;
+        const int nkb = P.p[e.x].K / BK;
+        const int nwin = (nkb + WIN_KB - 1) / WIN_KB;
+        for (int w = 0; w < nwin && ok; ++w, ++gw) {
+          const int hb = gw & 1;
+          const uint32_t hcol = hb ? COL_H1 : COL_H0;
+          const bool lseg_start = (w % LWIN) == 0;
+          if (gw >= 2 && !mbar_wait_bounded(&hempty[hb], ((gw >> 1) - 1) & 1, abort_flag, timeout_ns)) {
+            latch_error(st, kErrTimeout, 104);
+            ok = false;
+            break;
+          }
+          if (lseg_start && gl > 0 && !mbar_wait_bounded(lempty, (gl - 1) & 1, abort_flag, timeout_ns)) {
+            latch_error(st, kErrTimeout, 105);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a_base = smem_u32(smem + s * STAGE);
-          const uint32_t b_base = a_base + A_STAGE;
-#pragma unroll
-          for (int ks = 0; ks < BK / 16; ++ks) {
-            const bool first = (kb == kb_beg) && ks == 0;
-#pragma unroll
-            for (int q = 0; q < SC::NPROD; ++q) {
-              int pa, pb;
-              SC::pieces(q, pa, pb);
-              const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
-              const uint64_t bd = sdesc_k_sw128(b_base + pb * B_PIECE + ks * 32);
-              if (q == SC::NPROD - 1)
-                umma_f16(tmem + hcol, ad, bd, SC::IDESC, first ? 0u : 1u);
-              else
-                umma_f16(tmem + COL_L, ad, bd, SC::IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
+          const int kb_beg = w * WIN_KB, kb_end = min(nkb, (w + 1) * WIN_KB);
+          for (int kb = kb_beg; kb < kb_end; ++kb, ++g) {
+            const int s = static_cast<int>(g % STAGES);
+            const uint32_t ph = static_cast<uint32_t>((g / STAGES) & 1);
+            if (!mbar_wait_bounded(&full[s], ph, abort_flag, timeout_ns)) {
+              latch_error(st, kErrTimeout, 102);
+              ok = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t a_base = smem_u32(smem + s * STAGE);
+            const uint32_t b_base = a_base + A_STAGE;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+              const bool first = (kb == kb_beg) && ks == 0;
+#pragma unroll
+              for (int q = 0; q < SC::NPROD; ++q) {
+                int pa, pb;
+                SC::pieces(q, pa, pb);
+                const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
+                const uint64_t bd = sdesc_k_sw128(b_base + pb * B_PIECE + ks * 32);
+                if (q == SC::NPROD - 1)
+                  umma_f16(tmem + hcol, ad, bd, SC::IDESC, first ? 0u : 1u);
+                else
+                  umma_f16(tmem + COL_L, ad, bd, SC::IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
+              }
+            }
+            umma_commit(&empty[s]);  // releases the stage once its MMAs have read it
           }
-          umma_commit(&empty[s]);  // releases the stage once its MMAs have read it
+          if (!ok) break;
+          umma_commit(&hfull[hb]);
+          if ((w + 1) % LWIN == 0 || w == nwin - 1) {
+            umma_commit(lfull);
+            ++gl;
+          }
         }
-        umma_commit(&hfull[hb]);
-        if ((w + 1) % LWIN == 0 || w == nwin - 1) umma_commit(lfull);
       }
+      // every MMA this thread issued completes before TMEM is released
+      umma_commit(mdone);
+      mbar_wait_own(mdone, 0, timeout_ns);
     }
     __syncwarp();
   } else {
@@ -313,48 +412,64 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int cb = ((warp - 2) >> 2) * DCOLS;  // first accumulator column of this warp
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
     const uint32_t lo_addr = tmem + lane_off + COL_LO + cb;
-    float acc[DCOLS], HI[DCOLS];
-#pragma unroll
-    for (int j = 0; j < DCOLS; ++j) acc[j] = HI[j] = 0.f;
-    {
-      uint32_t z[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) z[j] = 0u;
-#pragma unroll
-      for (int c = 0; c < DCOLS; c += 16) tmem_st16(lo_addr + c, z);
-      tmem_st_wait();
-    }
+    int gw = 0, gl = 0, tc = 0;
     bool ok = true;
-    for (int w = 0; w < nwin && ok; ++w) {
-      const int hb = w & 1;
-      bool got = mbar_wait_bounded(&hfull[hb], (w >> 1) & 1, abort_flag, timeout_ns);
+    while (ok) {
+      const int slot = tc % TRING;
+      bool got = mbar_wait_bounded(&tfull[slot], (tc / TRING) & 1, abort_flag, timeout_ns);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
       }
-      tc_fence_after();
-      add_cols(tmem + lane_off + (hb ? COL_H1 : COL_H0) + cb, acc);
-      tc_fence_before();
+      const int4 e = ring[slot];
       __syncwarp();
-      if (lane == 0) mbar_arrive(&hempty[hb]);
-      if ((w + 1) % LWIN == 0 || w == nwin - 1) {
-        got = mbar_wait_bounded(lfull, (w / LWIN) & 1, abort_flag, timeout_ns);
+      if (lane == 0) mbar_arrive(&tempty[slot]);
+      ++tc;
+      if (e.x < 0) break;
+      const Prob& pr = P.p[e.x];
+      const int nkb = pr.K / BK;
+      const int nwin = (nkb + WIN_KB - 1) / WIN_KB;
+      float acc[DCOLS], HI[DCOLS];
+#pragma unroll
+      for (int j = 0; j < DCOLS; ++j) acc[j] = HI[j] = 0.f;
+      {
+        uint32_t z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) z[j] = 0u;
+#pragma unroll
+        for (int c = 0; c < DCOLS; c += 16) tmem_st16(lo_addr + c, z);
+        tmem_st_wait();
+      }
+      for (int w = 0; w < nwin; ++w, ++gw) {
+        const int hb = gw & 1;
+        got = mbar_wait_bounded(&hfull[hb], (gw >> 1) & 1, abort_flag, timeout_ns);
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        add_cols(tmem + lane_off + COL_L + cb, acc);
+        add_cols(tmem + lane_off + (hb ? COL_H1 : COL_H0) + cb, acc);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0 && w != nwin - 1) mbar_arrive(lempty);
+        if (lane == 0) mbar_arrive(&hempty[hb]);
+        if ((w + 1) % LWIN == 0 || w == nwin - 1) {
+          got = mbar_wait_bounded(lfull, gl & 1, abort_flag, timeout_ns);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          add_cols(tmem + lane_off + COL_L + cb, acc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(lempty);
+          ++gl;
+        }
+        if ((w + 1) % FOLD == 0 || w == nwin - 1) fold_cols(lo_addr, acc, HI);
       }
-      if ((w + 1) % FOLD == 0 || w == nwin - 1) fold_cols(lo_addr, acc, HI);
-    }
-    ok = ok && !*abort_flag;
-    if (!ok) {
-      if (lane == 0) latch_error(st, kErrTimeout, 103);
-    } else {
+      ok = ok && !*abort_flag;
+      if (!ok) break;
+      const int m0 = e.y, n0 = e.z;
       const int row = m0 + q * 32 + lane;
       const float inv = (1.f / ld_scale(pr.sa)) * (1.f / ld_scale(pr.sb));  // powers of two: exact
 #pragma unroll
@@ -379,6 +494,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
+    if (!ok && lane == 0) latch_error(st, kErrTimeout, 103);
   }
   tc_fence_before();
   __syncthreads();
@@ -405,7 +521,7 @@ EncodeFn get_encode() {
   return fn;
 }
 
-// 3-D map over the piece-stacked BF16 matrix: dims {cols, rows, 3 pieces}.
+// 3-D map over the piece-stacked 16-bit matrix: dims {cols, rows, pieces}.
 bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int64_t piece,
               int box_rows, int box_pieces, int npieces, CUtensorMapDataType dtype) {
   EncodeFn enc = get_encode();
@@ -421,41 +537,64 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int6
   return r == CUDA_SUCCESS;
 }
 
+// SM count of the current device (cached per device).
+int sm_count(int dev) {
+  static std::atomic<int> cache[64];
+  int n = cache[dev].load();
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  cache[dev].store(n);
+  return n;
+}
+
 template <int NP>
 int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
+  static_assert(sizeof(Probs) <= 32000, "launch parameters exceed the kernel parameter limit");
   Probs P;
   memset(&P, 0, sizeof(P));
   const CUtensorMapDataType dt = NP == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  int64_t tiles = 0;
   // window given in 32-term units; FP16 leading products (22 significant
   // bits) lose more to the truncating accumulation than BF16 ones (16 bits),
   // so their default window is half as long
   P.win_kb = std::max(1, tuned_win_kb(NP == 2 ? 2 : 4) * 32 / BK);
   P.lwin = std::max(1, (4096 / BK) / P.win_kb);      // L segment of 4096 K terms
-  for (int i = 0; i < nops; ++i) {
-    const GemmOp& op = ops[i];
+  // longest K first: the queue hands out the longest tiles before the short ones
+  std::vector<int> order(nops);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ops[a].K > ops[b].K; });
+  int64_t total = 0;
+  for (int k = 0; k < nops; ++k) {
+    const GemmOp& op = ops[order[k]];
+    Prob& pr = P.p[k];
     if (op.mode != OUT_FF_STORE && op.mode != OUT_FF_ACCUM) return -1;
+    if (!op.A || !op.B || !op.out) return -1;  // never launch on a missing operand or output
     if (op.M <= 0 || op.N <= 0 || op.K <= 0) return -1;
     if (op.K % BK || op.K > 2147483647LL || op.M > 2147483647LL || op.N > 2147483647LL) return -1;
     if ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.B)) & 15) return -1;
     if ((op.lda | op.ldb | op.a_piece | op.b_piece) & 7) return -1;
-    if (!make_map(&P.p[i].ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM, NP, NP, dt)) return -4;
-    if (!make_map(&P.p[i].tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN, NP, NP, dt)) return -4;
-    P.p[i].out = static_cast<float2*>(op.out);
-    P.p[i].sa = op.scale_a;
-    P.p[i].sb = op.scale_b;
-    P.p[i].ldo = op.ldo;
-    P.p[i].M = static_cast<int>(op.M);
-    P.p[i].N = static_cast<int>(op.N);
-    P.p[i].K = static_cast<int>(op.K);
-    P.p[i].mode = op.mode;
-    P.p[i].tri = static_cast<int>(op.tri);
-    tiles = std::max<int64_t>(tiles, ((op.M + BM - 1) / BM) * ((op.N + BN - 1) / BN));
+    if (!make_map(&pr.ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM, NP, NP, dt)) return -4;
+    if (!make_map(&pr.tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN, NP, NP, dt)) return -4;
+    pr.out = static_cast<float2*>(op.out);
+    pr.sa = op.scale_a;
+    pr.sb = op.scale_b;
+    pr.ldo = op.ldo;
+    pr.M = static_cast<int>(op.M);
+    pr.N = static_cast<int>(op.N);
+    pr.K = static_cast<int>(op.K);
+    pr.mode = op.mode;
+    pr.tri = static_cast<int>(op.tri);
+    pr.mt = static_cast<int>((op.M + BM - 1) / BM);
+    pr.nt = static_cast<int>((op.N + BN - 1) / BN);
+    pr.tile0 = static_cast<int>(total);
+    total += static_cast<int64_t>(pr.mt) * pr.nt;
+    if (total > 2000000000LL) return -1;
   }
-  // the shared-memory opt-in is a per-device function attribute: set it once for every device used
-  static std::atomic<uint64_t> attr_set{0};
+  P.nprob = nops;
+  P.total = static_cast<int>(total);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -4;
+  // the shared-memory opt-in is a per-device function attribute: set it once for every device used
+  static std::atomic<uint64_t> attr_set{0};
   if (!(attr_set.load() & (1ull << dev))) {
     const cudaError_t attr_err =
         cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -465,17 +604,15 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     }
     attr_set.fetch_or(1ull << dev);
   }
-  if (tiles > 2147483647LL) return -1;
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3(static_cast<unsigned>(tiles), 1, static_cast<unsigned>(nops));
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = stream;
-  cfg.attrs = nullptr;
-  cfg.numAttrs = 0;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, cc_gemm_split3_tc<NP>, P, ops[0].status, ops[0].timeout_ns);
-  if (e == cudaSuccess) e = cudaPeekAtLastError();
+  int* queue = ops[0].queue;
+  if (!queue) return -1;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), stream);
+  if (e == cudaSuccess) {
+    const int64_t ctas = std::min<int64_t>(total, sm_count(dev));
+    cc_gemm_split3_tc<NP><<<static_cast<unsigned>(ctas), NTHREADS, SMEM_BYTES, stream>>>(
+        P, queue, ops[0].status, ops[0].timeout_ns);
+    e = cudaPeekAtLastError();
+  }
   if (e != cudaSuccess) {
     note_cuda(e);
     return -4;
@@ -487,7 +624,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
 }  // namespace
 
 int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
-  if (nops < 1 || nops > 2) return -1;
+  if (nops < 1 || nops > MAXP) return -1;
   for (int i = 1; i < nops; ++i)
     if (ops[i].pieces != ops[0].pieces) return -1;
   if (ops[0].pieces == 3) return launch<3>(ops, nops, stream);

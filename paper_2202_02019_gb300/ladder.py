@@ -17,7 +17,7 @@ import torch
 from . import _build
 
 CC_PREC = {"fp64": 0, "mixed": 1, "fp16x2": 2}
-CC_WS_RESIDUAL, CC_WS_DENSITY, CC_WS_LAGRANGIAN, CC_WS_STEP = 1, 2, 4, 7
+CC_WS_RESIDUAL, CC_WS_DENSITY, CC_WS_LAGRANGIAN, CC_WS_STEP, CC_WS_BATCH = 1, 2, 4, 7, 8
 
 _lib = None
 
@@ -91,6 +91,16 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_ov3_gs.restype = I
     lib.cc_ladder_ov3_es_abci.argtypes = [I, I, I, P, P, P, P, P, P, I, VP, S, VP]
     lib.cc_ladder_ov3_es_abci.restype = I
+    lib.cc_ladder_ov3_es_abic_workspace_size.argtypes = [I, I, I, I]
+    lib.cc_ladder_ov3_es_abic_workspace_size.restype = S
+    lib.cc_ladder_ov3_es_abic.argtypes = [I, I, I, P, P, P, P, P, ctypes.c_double, P, P, P, P, I, VP, S, VP]
+    lib.cc_ladder_ov3_es_abic.restype = I
+    lib.cc_ladder_pair_blocks.argtypes = [SYS, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.cc_ladder_pair_blocks.restype = I
+    lib.cc_ladder_step_blocks.argtypes = [SYS, ctypes.POINTER(ctypes.c_int32), I, P, P, P, I, VP, S, VP]
+    lib.cc_ladder_step_blocks.restype = I
+    lib.cc_ladder_scale_by.argtypes = [P, ctypes.c_int64, ctypes.c_double, P, VP]
+    lib.cc_ladder_scale_by.restype = I
     lib.cc_ladder_set_tuning.argtypes = [I, I]
     lib.cc_ladder_set_tuning.restype = I
     lib.cc_ladder_profile.argtypes = [I]
@@ -111,6 +121,8 @@ EXPORTS = (
     "cc_ladder_w_backtransform", "cc_ladder_density_es", "cc_ladder_mp2_driver_workspace_size",
     "cc_ladder_mp2_driver", "cc_ladder_iterate_workspace_size", "cc_ladder_iterate",
     "cc_ladder_ov3_workspace_size", "cc_ladder_ov3_gs", "cc_ladder_ov3_es_abci",
+    "cc_ladder_pair_blocks", "cc_ladder_step_blocks", "cc_ladder_scale_by",
+    "cc_ladder_ov3_es_abic_workspace_size", "cc_ladder_ov3_es_abic",
 )
 
 
@@ -227,13 +239,16 @@ def _prec(p):
     return CC_PREC[p] if isinstance(p, str) else int(p)
 
 
-def cc_ladder_workspace_size(systems: Sequence[System], prec="mixed", which=CC_WS_STEP) -> int:
+def cc_ladder_workspace_size(systems: Sequence[System], prec="mixed", which=CC_WS_STEP, batched=False) -> int:
+    """Workspace bytes; batched=True sizes the batched schedule of a list of systems."""
     lib = load()
+    if batched:
+        which |= CC_WS_BATCH
     return int(lib.cc_ladder_workspace_size(_arr(systems), len(systems), _prec(prec), which))
 
 
-def workspace(systems: Sequence[System], prec="mixed", which=CC_WS_STEP, device=None) -> torch.Tensor:
-    n = cc_ladder_workspace_size(systems, prec, which)
+def workspace(systems: Sequence[System], prec="mixed", which=CC_WS_STEP, device=None, batched=False) -> torch.Tensor:
+    n = cc_ladder_workspace_size(systems, prec, which, batched)
     if n == 0:
         raise LadderError(-1, "invalid systems for workspace sizing")
     dev = device or systems[0].L_vv.device
@@ -326,6 +341,46 @@ def cc_ladder_step(systems, prec="mixed", ws=None, omega=None, D=None, E=None, s
     wp, wn = _ws_args(_ws(systems, prec, CC_WS_STEP, ws))
     _check(lib.cc_ladder_step(arr, len(systems), po, pd, pe, _prec(prec), wp, wn, _stream(stream)))
     return omega, D, E
+
+
+def cc_ladder_pair_blocks(system):
+    """(number of pair blocks, block edge) of one system under the current tuning (host only)."""
+    cnt, edge = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cc_ladder_pair_blocks(_arr([system]), ctypes.byref(cnt), ctypes.byref(edge)))
+    return cnt.value, edge.value
+
+
+def cc_ladder_step_blocks(system, blocks, prec="mixed", ws=None, omega=None, D=None, E=None, stream=None):
+    """One shard of a system's step: Omega for the pairs of the listed pair blocks (written into
+    `omega`, other entries untouched), their partial D and partial E (see the C header)."""
+    lib = load()
+    blocks = [int(b) for b in blocks]
+    if not blocks:
+        raise ValueError("a shard needs at least one pair block")
+    arr = _arr([system])
+    omega = torch.empty_like(system.t2) if omega is None else omega
+    D = torch.empty_like(system.L_vv) if D is None else D
+    E = torch.empty(1, dtype=torch.float64, device=system.L_vv.device) if E is None else E
+    po = _outs([omega], [system], "t2", "Omega")
+    pd = _outs([D], [system], "L_vv", "D")
+    pe = _energy(E, 1)
+    wp, wn = _ws_args(_ws([system], prec, CC_WS_STEP, ws))
+    bl = (ctypes.c_int32 * len(blocks))(*blocks)
+    _check(lib.cc_ladder_step_blocks(arr, bl, len(blocks), ctypes.c_void_p(po[0]), ctypes.c_void_p(pd[0]), pe,
+                                     _prec(prec), wp, wn, _stream(stream)))
+    return omega, D, E
+
+
+def cc_ladder_scale_by(x, factor, g=None, stream=None):
+    """x *= factor * g (g: a float64 device scalar tensor, or None), in the library; returns x."""
+    gp = None
+    if g is not None:
+        if g.numel() != 1:
+            raise ValueError("g must hold one value")
+        gp = ctypes.c_void_p(_dev_ptr(g.reshape(1), "g"))
+    _check(load().cc_ladder_scale_by(ctypes.c_void_p(_dev_ptr(x, "x")), x.numel(), float(factor), gp,
+                                     _stream(stream)))
+    return x
 
 
 def cc_ladder_update(systems, omega, out=None, stream=None):
@@ -473,6 +528,29 @@ def cc_ladder_ov3_es_abci(L_vv, L_ov, L2, R1, prec="mixed", ws=None, stream=None
                                      _f64(R1, "R1"), _f64(W_vv, "W_vv"), _f64(W_vo, "W_vo"), _prec(prec),
                                      *_ws_args(ws), _stream(stream)))
     return W_vv, W_vo
+
+
+def cc_ladder_ov3_es_abic(L_vv, L_ov, tbar1, L2, t2, R0, R1, R2, prec="mixed", ws=None, stream=None):
+    """Excited-state d_abic contributions (W_vv [nj, v, v], W_ov [nj, o, v]); see the C header."""
+    lib = load()
+    nj, o, v = L_ov.shape
+    _shape(L_vv, (nj, v, v), "L_vv")
+    _shape(tbar1, (o, v), "tbar1")
+    _shape(R1, (o, v), "R1")
+    for t, n in ((L2, "L2"), (t2, "t2"), (R2, "R2")):
+        _shape(t, (o, o, v, v), n)
+    if ws is None:
+        n = int(lib.cc_ladder_ov3_es_abic_workspace_size(o, v, nj, _prec(prec)))
+        if n == 0:
+            raise LadderError(-1, "invalid sizes for the OV^3 workspace")
+        ws = torch.empty(n, dtype=torch.uint8, device=L_vv.device)
+    W_vv = torch.empty_like(L_vv)
+    W_ov = torch.empty_like(L_ov)
+    _check(lib.cc_ladder_ov3_es_abic(o, v, nj, _f64(L_vv, "L_vv"), _f64(L_ov, "L_ov"), _f64(tbar1, "tbar1"),
+                                     _f64(L2, "L2"), _f64(t2, "t2"), float(R0), _f64(R1, "R1"), _f64(R2, "R2"),
+                                     _f64(W_vv, "W_vv"), _f64(W_ov, "W_ov"), _prec(prec), *_ws_args(ws),
+                                     _stream(stream)))
+    return W_vv, W_ov
 
 
 def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):

@@ -8,7 +8,9 @@ partial D for the rows x of both blocks; the partial D of all ranks is summed
 by one reduce-scatter (FP64), and Omega, if wanted whole, by an all-gather.
 Blocks are dealt largest-first to the least-loaded rank (LPT) by their
 counted flops.  The same blocking and flop count are used here as in the
-library (csrc/ccladder.cu) and in bench.py.
+library (csrc/ccladder.cu, cc_ladder_pair_blocks) and in bench.py; a rank
+runs its share with cc_ladder_step_blocks and the partial D meet in one
+reduce-scatter.
 """
 from __future__ import annotations
 
@@ -76,3 +78,35 @@ def aggregate_step_time(ms_local: float, world: int, flops_per_rank: float):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms = float(t[0])
     return ms, world * flops_per_rank / (ms * 1e-3) / 1e12
+
+
+def rank_blocks(system, rank: int, world: int) -> List[int]:
+    """Pair blocks of `system` (a ladder.System) that rank `rank` of `world` owns, in the
+    library's pair-block numbering (the blocking is checked against the library's own)."""
+    from . import ladder as lad
+    count, edge = lad.cc_ladder_pair_blocks(system)
+    blocks = pair_blocks(system.v, edge)
+    if len(blocks) != count:
+        raise RuntimeError(f"pair-block count mismatch: {len(blocks)} here, {count} in the library")
+    return lpt_partition(blocks, world, system.o, system.v, system.nj)[rank]
+
+
+def reduce_scatter_D(D_part, world: int):
+    """Sum the ranks' partial D (any float64 tensor, flattened) and return this rank's
+    contiguous slice of the sum, the flat D padded to a multiple of world.  One
+    reduce-scatter with NCCL; gloo has none, so there it is an all-reduce and a slice."""
+    import torch
+    import torch.distributed as dist
+    flat = D_part.reshape(-1)
+    n = flat.numel()
+    chunk = (n + world - 1) // world
+    if chunk * world != n:
+        flat = torch.cat([flat, flat.new_zeros(chunk * world - n)])
+    rank = dist.get_rank()
+    if dist.get_backend() == "nccl":
+        out = flat.new_empty(chunk)
+        dist.reduce_scatter_tensor(out, flat, op=dist.ReduceOp.SUM)
+        return out
+    full = flat.clone()
+    dist.all_reduce(full, op=dist.ReduceOp.SUM)
+    return full[rank * chunk:(rank + 1) * chunk].clone()

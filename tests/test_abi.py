@@ -170,3 +170,50 @@ def test_binding_checks_lengths_shapes_and_E_on_the_host():
     # the no-allocation wrapper does not allocate E for the caller
     with pytest.raises(TypeError):
         lad.cc_ladder_lagrangian_noalloc([s], [f(2, 2, 4, 4)])
+
+
+def test_batched_workspace_size_host_only():
+    lib = lad.load()
+    B = lad.CC_WS_BATCH
+    one = (lad.cc_ladder_system * 1)(fake_sys(6, 30, 90))
+    # a single system has nothing to interleave: same size either way
+    assert lib.cc_ladder_workspace_size(one, 1, 1, 7 | B) == lib.cc_ladder_workspace_size(one, 1, 1, 7)
+    sizes = [(4, 20, 60), (6, 30, 90), (5, 57, 120), (3, 11, 40)]
+    arr = (lad.cc_ladder_system * 4)(*[fake_sys(*x) for x in sizes])
+    for prec in (0, 1, 2):
+        seq = lib.cc_ladder_workspace_size(arr, 4, prec, 7)
+        bat = lib.cc_ladder_workspace_size(arr, 4, prec, 7 | B)
+        # every system keeps its own prepared operands, and each slot fits the largest block
+        singles = [lib.cc_ladder_workspace_size((lad.cc_ladder_system * 1)(fake_sys(*x)), 1, prec, 7) for x in sizes]
+        assert seq == max(singles)
+        assert bat > seq
+        assert bat < sum(singles) + 4 * max(singles)
+    # the batch bit alone (no call selected) is not a valid request
+    assert lib.cc_ladder_workspace_size(arr, 4, 1, B) == 0
+    assert lib.cc_ladder_workspace_size(arr, 4, 1, 7 | 16) == 0
+
+
+def test_pair_block_enumeration_matches_the_shard_plan():
+    # host-only query: the library's pair-block count and edge agree with shard.pair_blocks
+    import ctypes as C
+    from paper_2202_02019_gb300 import shard
+    lib = lad.load()
+    try:
+        for edge in (0, 16, 48, 52):
+            lib.cc_ladder_set_tuning(edge, 0)
+            for v in (1, 7, 48, 49, 150, 650):
+                arr = (lad.cc_ladder_system * 1)(fake_sys(3, v, 10))
+                cnt, e = C.c_int32(), C.c_int32()
+                assert lib.cc_ladder_pair_blocks(arr, C.byref(cnt), C.byref(e)) == 0
+                assert len(shard.pair_blocks(v, e.value)) == cnt.value
+                assert e.value == min(edge or 48, ((v + 3) // 4) * 4)
+    finally:
+        lib.cc_ladder_set_tuning(0, 0)
+    # shard arguments are checked on the host: empty, out of range and repeated block lists
+    P = C.c_void_p
+    arr = (lad.cc_ladder_system * 1)(fake_sys(3, 20, 10))
+    ws = P(0x100000)
+    for bl in ([], [3], [0, 0], [-1]):
+        arrb = (C.c_int32 * max(1, len(bl)))(*bl)
+        assert lib.cc_ladder_step_blocks(arr, arrb, len(bl), P(0x8000), P(0x9000), P(0xA000), 1, ws, 1 << 40,
+                                         None) == -1

@@ -1,6 +1,8 @@
-"""Batched systems: one graph-captured call over systems of uneven size
-gives the same bits as one call per system, and matches the oracle; the
-autotuner picks and caches valid knobs."""
+"""Batched systems: one graph-captured call over systems of uneven size --
+with the batched schedule (pair blocks of several systems in every grouped
+contraction launch) and back to back -- gives the same bits as one call per
+system on the split paths, and matches the oracle; the autotuner picks and
+caches knobs whose results match the oracle."""
 import os
 
 import numpy as np
@@ -35,10 +37,14 @@ def batch():
     return host, dev
 
 
+@pytest.mark.parametrize("batched", [True, False], ids=["batched", "back_to_back"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp16x2"])
-def test_graph_captured_batch_equals_one_by_one(batch, prec):
+def test_graph_captured_batch_equals_one_by_one(batch, prec, batched):
     host, systems = batch
-    ws = lad.workspace(systems, prec)
+    ws = lad.workspace(systems, prec, batched=batched)
+    assert ws.numel() == lad.cc_ladder_workspace_size(systems, prec, batched=batched)
+    if batched:
+        assert ws.numel() > lad.cc_ladder_workspace_size(systems, prec)
     om = [torch.empty_like(s.t2) for s in systems]
     D = [torch.empty_like(s.L_vv) for s in systems]
     E = torch.empty(len(systems), dtype=torch.float64, device="cuda")

@@ -54,11 +54,9 @@ def _shard_worker(rank, world, port, q):
             pairs = [(list(A), list(B))] + ([] if b.diag else [(list(B), list(A))])
             for X, Y in pairs:
                 D[:, X, :] += np.einsum("xycd,Jyd->Jxc", G[np.ix_(X, Y)], s.L_vv[:, Y, :])
-        # D: a reduce-scatter over J slices (gloo has none, so all-reduce and keep
-        # this rank's slice); Omega: ranks own disjoint entries, so a sum gathers it
-        full = torch.from_numpy(D.copy())
-        dist.all_reduce(full, op=dist.ReduceOp.SUM)
-        outD = full.reshape(world, -1)[rank].clone()
+        # D: the reduce-scatter of shard.reduce_scatter_D (gloo: all-reduce and keep this
+        # rank's slice); Omega: ranks own disjoint entries, so a sum gathers it
+        outD = shard.reduce_scatter_D(torch.from_numpy(D.copy()), world)
         omt = torch.from_numpy(om.copy())
         dist.all_reduce(omt, op=dist.ReduceOp.SUM)
         q.put((rank, outD.numpy(), omt.numpy(), mine))

@@ -1,15 +1,22 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Tolerances (relative Frobenius error; E: relative error):
-  FP64 path   Omega, D <= 1e-11, E <= 1e-11
-  mixed paths Omega, D <= 1e-6,  E <= 1e-6  (split-BF16 and scaled split-FP16)
+  FP64 path   Omega, D <= 1e-11, E <= 1e-11 (the Lagrangian target is 1e-9)
+  mixed paths Omega, D <= 1e-6 (split-BF16 and scaled split-FP16)
 The FP64 path only reorders FP64 sums (K-chunked DMMA, atomics), so it
 sits near 1e-15.  The split paths carry 24-bit (three BF16 pieces) or 22-bit
 (two scaled FP16 pieces) operands; the tensor core's FP32 accumulation
 truncates, so the leading piece product is re-started every 128 (BF16) or
 64 (FP16) K terms and the window sums are added without drift, which leaves
-a small coherent bias toward zero (2-6e-7 on these cases).  E inherits that
-bias from Omega, so it is held to the same 1e-6 as Omega.
+a small coherent bias toward zero (2-6e-7 on these cases).
+
+E on the split paths: the target is 1e-9 relative, asserted by
+test_split_lagrangian_target, which is expected to fail (xfail) with the
+measured error: E inherits Omega's coherent truncation bias whole, 3-6e-7
+here.  The operand format alone would reach it (tests/test_split_floor.py
+emulates the three-piece split with exact sums: E to <= 4.3e-10); the
+tensor core's truncating FP32 accumulation does not.  The step tests keep E
+within 1e-6 as a guard against gross errors, not as the target.
 """
 import numpy as np
 import pytest
@@ -22,7 +29,8 @@ from paper_2202_02019_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-11, "mixed": 1e-6, "fp16x2": 1e-6}
-TOL_E = {"fp64": 1e-11, "mixed": 1e-6, "fp16x2": 1e-6}
+TOL_E = {"fp64": 1e-11, "mixed": 1e-6, "fp16x2": 1e-6}   # split paths: a guard, not the 1e-9 target
+E_TARGET = 1e-9
 
 
 def rel(a, b):
@@ -165,3 +173,24 @@ def test_bounded_wait_times_out_and_recovers():
     om = lad.cc_ladder_residual([dev_sys(s, tb2)], prec="mixed")
     torch.cuda.synchronize()
     assert rel(om[0].cpu(), om_ref) < TOL["mixed"]
+
+
+@pytest.mark.xfail(reason="split paths: E carries the tensor core's truncation bias (3-6e-7), "
+                          "above the 1e-9 Lagrangian target; the FP64 path meets it", strict=False)
+@pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
+@pytest.mark.parametrize("name", ["tiny_4_20_60", "ragged_5_37_70", "fd_8_48_160"])
+def test_split_lagrangian_target(name, prec):
+    s, tb2, om_ref, D_ref, E_ref = ref(name)
+    om, D, E = lad.cc_ladder_step([dev_sys(s, tb2)], prec=prec)
+    torch.cuda.synchronize()
+    ee = abs(float(E[0]) - E_ref) / abs(E_ref)
+    print(f"{name} {prec}: E rel err {ee:.2e} (target {E_TARGET:.0e})")
+    assert ee <= E_TARGET, ee
+
+
+@pytest.mark.parametrize("name", ["tiny_4_20_60", "ragged_5_37_70", "fd_8_48_160"])
+def test_fp64_lagrangian_target(name):
+    s, tb2, om_ref, D_ref, E_ref = ref(name)
+    om, D, E = lad.cc_ladder_step([dev_sys(s, tb2)], prec="fp64")
+    torch.cuda.synchronize()
+    assert abs(float(E[0]) - E_ref) <= E_TARGET * abs(E_ref)
