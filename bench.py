@@ -482,14 +482,14 @@ def run_batch(args):
         return e0.elapsed_time(e1) / args.steps
 
     ms_seq = timed(one_by_one)
-    ref = [x.clone() for x in om[:2]]
+    ref = [x.clone() for x in om + D] + [E.clone()]
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         lad.cc_ladder_step(systems, prec=args.prec, ws=ws, omega=om, D=D, E=E)
     n0 = lad.cc_ladder_launch_count()
     with Clocks(0) as clk:
         ms_graph = timed(g.replay)
-    same = all(torch.equal(a, b) for a, b in zip(ref, om[:2]))
+    same = all(torch.equal(a, b) for a, b in zip(ref, om + D + [E]))
     line = {
         "metric": "ladder Omega + D^J useful TFLOP/s, 24-system uneven batch (mixed path)",
         "value": F / (ms_graph * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,

@@ -31,7 +31,13 @@
  *     aligned, at least cc_ladder_workspace_size() bytes).  Calls that share
  *     a workspace must be ordered on one stream.
  *   - `stream` is a cudaStream_t (NULL: legacy default stream).  Calls are
- *     asynchronous; host-detectable argument errors are returned at once,
+ *     asynchronous.  Calls that compute both Omega and D (cc_ladder_step,
+ *     cc_ladder_step_blocks) run the density chain on one internal stream per
+ *     device, created on the first such call with that device current (make
+ *     it before any stream capture), forked from `stream` after the
+ *     preparation and joined back to it before the call's last kernels; work
+ *     enqueued on `stream` afterwards sees all of the call's results.
+ *     Host-detectable argument errors are returned at once,
  *     device-side errors (bounded waits that gave up) are latched in the
  *     workspace and reported by cc_ladder_status().  Each call clears the
  *     latched status at its start, so read it after the call it concerns.
@@ -354,7 +360,9 @@ long long cc_ladder_launch_count(void);
 /* Instrumentation (not part of the paper's method).  cc_ladder_profile(1)
  * makes every later call record a CUDA event pair on its stream around each
  * tensor-core contraction launch; cc_ladder_profile_read() waits for the
- * recorded events and returns the summed contraction time in milliseconds,
+ * recorded events and returns the contraction time in milliseconds (the length
+ * of the union of the launches' intervals: launches on the library's second
+ * stream may overlap those on the caller's),
  * the number of contraction launches and their padded 2*M*N*K flop count,
  * then clears them.  cc_ladder_profile(0) switches recording off. */
 void cc_ladder_profile(int enable);

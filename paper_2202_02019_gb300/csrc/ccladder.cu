@@ -694,11 +694,14 @@ struct Plan {
   // intermediates of one pair block in flight).  0 = not present.
   size_t s_scl = 0;  // FP16 path: operand bounds (8 x u32) at +0, scales (5 floats) at +64 (always present)
   size_t s_tp = 0, s_tm = 0, s_LT = 0, s_LN = 0, s_tpT = 0, s_tmT = 0, s_bp = 0, s_bm = 0, s_D = 0, s_E = 0;
-  // A scratch slot has two parts: operand pieces (g+-, the Gamma slabs) first, then float-float (or
-  // FP64) scratch (G, Omega+-, Gamma+-).  Slot offsets are relative to the start of their part.
-  size_t k_gp = 0, k_gm = 0, k_Gt = 0, k_Gb = 0;               // piece part
-  size_t k_G = 0, k_Op = 0, k_Om = 0, k_Gp = 0, k_Gm = 0;      // scratch part
-  size_t sys_bytes = 0, piece_bytes = 0, scratch_bytes = 0;
+  // A scratch slot has four parts: for each of the two chains (residual, density) its operand pieces
+  // (g+-; the Gamma slabs) and its float-float (or FP64) scratch (G, Omega+-; Gamma+-).  Slot offsets
+  // are relative to the start of their part.
+  size_t k_gp = 0, k_gm = 0;              // residual pieces
+  size_t k_G = 0, k_Op = 0, k_Om = 0;     // residual scratch
+  size_t k_Gt = 0, k_Gb = 0;              // density pieces
+  size_t k_Gp = 0, k_Gm = 0;              // density scratch
+  size_t sys_bytes = 0, part[4] = {0, 0, 0, 0};  // bytes of: residual pieces, residual scratch, density ...
 };
 
 constexpr size_t kStatusBytes = 256;
@@ -756,7 +759,7 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
   const bool res = which & (CC_WS_RESIDUAL | CC_WS_LAGRANGIAN);
   const bool den = which & CC_WS_DENSITY;
   // every region starts past a 256-byte gap, so that offset 0 means "not present" in each
-  size_t sys = 256, pcs = 256, scr = 256;
+  size_t sys = 256, rp = 256, rs = 256, dp = 256, ds = 256;
   auto take = [](size_t& cur, size_t bytes) {
     const size_t at = cur;
     cur += rup(static_cast<int64_t>(bytes), 256);
@@ -768,11 +771,11 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
   P.s_tm = take(sys, mat_bytes(pr, P.Pom, P.Kvm));
   if (res) {
     P.s_LT = take(sys, mat_bytes(pr, v * v, P.Kj));
-    P.k_G = take(scr, static_cast<size_t>(P.maxrows) * P.maxrows * 8);
-    P.k_gp = take(pcs, mat_bytes(pr, P.maxpairs, P.Kvp));
-    P.k_gm = take(pcs, mat_bytes(pr, P.maxpairs, P.Kvm));
-    P.k_Op = take(scr, static_cast<size_t>(P.Pop) * P.ldO * 8);
-    P.k_Om = take(scr, static_cast<size_t>(P.Pom) * P.ldO * 8);
+    P.k_G = take(rs, static_cast<size_t>(P.maxrows) * P.maxrows * 8);
+    P.k_gp = take(rp, mat_bytes(pr, P.maxpairs, P.Kvp));
+    P.k_gm = take(rp, mat_bytes(pr, P.maxpairs, P.Kvm));
+    P.k_Op = take(rs, static_cast<size_t>(P.Pop) * P.ldO * 8);
+    P.k_Om = take(rs, static_cast<size_t>(P.Pom) * P.ldO * 8);
   }
   if (den) {
     P.s_LN = take(sys, mat_bytes(pr, nj, v * P.vp));
@@ -781,15 +784,17 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
     P.s_bp = take(sys, mat_bytes(pr, P.Pvp, P.Kop));
     P.s_bm = take(sys, mat_bytes(pr, P.Pvp, P.Kom));
     if (prec != CC_PREC_FP64) P.s_D = take(sys, static_cast<size_t>(nj) * v * v * 8);  // float-float D
-    P.k_Gp = take(scr, static_cast<size_t>(P.maxpairs) * P.Kvp * 8);
-    P.k_Gm = take(scr, static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
-    P.k_Gt = take(pcs, mat_bytes(pr, P.maxrows, P.ldt));
-    P.k_Gb = take(pcs, mat_bytes(pr, P.maxrows, P.ldt));
+    P.k_Gp = take(ds, static_cast<size_t>(P.maxpairs) * P.Kvp * 8);
+    P.k_Gm = take(ds, static_cast<size_t>(P.maxpairs) * P.Kvm * 8);
+    P.k_Gt = take(dp, mat_bytes(pr, P.maxrows, P.ldt));
+    P.k_Gb = take(dp, mat_bytes(pr, P.maxrows, P.ldt));
   }
   P.s_E = take(sys, static_cast<size_t>(P.n_epart) * 8);
   P.sys_bytes = sys;
-  P.piece_bytes = pcs;
-  P.scratch_bytes = scr;
+  P.part[0] = rp;
+  P.part[1] = rs;
+  P.part[2] = dp;
+  P.part[3] = ds;
   return true;
 }
 
@@ -797,8 +802,8 @@ static bool make_plan(const cc_ladder_system& sy, int prec, int which, Plan& P) 
 // execution
 // ---------------------------------------------------------------------------
 // Workspace header (the first kStatusBytes bytes): the latched Status at 0,
-// the FP16 path's operand bounds at 64 and scales at 128, the contraction's
-// tile-queue counter at kQueueOffset.
+// the tile-queue counters of the contraction launches at kQueueOffset (the
+// caller's stream) and kQueueOffset + 4 (the density chain's stream).
 constexpr size_t kQueueOffset = 224;
 
 struct Ctx {
@@ -966,11 +971,14 @@ struct SysRun {
   std::vector<size_t> subset;  // non-empty: only these pair blocks (a shard of the system)
 };
 
-// One pair block in flight: the system, the block, the scratch slot it uses
-// (its operand-piece part and its float-float scratch part).
+// One pair block in flight: the system, the block, the scratch slot it uses.
+// A slot has one part per chain and kind (residual pieces, residual scratch,
+// density pieces, density scratch), each as large as the largest system of
+// the call needs: the two chains run on different streams, and a slot serves
+// different systems (with different layouts) in successive waves, so a
+// chain must never touch bytes the other chain may be using.
 struct Slot {
-  char* pieces;
-  char* scratch;
+  char* part[4];
 };
 struct Item {
   SysRun* r;
@@ -1085,97 +1093,53 @@ static void prep_system(const SysRun& R, bool do_res, bool do_den, Ctx& c) {
 }
 
 // The pair blocks of one wave (at most one per system, each with its own
-// scratch slot) through the four contractions.  Two grouped contraction
-// launches carry every block of the wave: the g-builds with the Gamma+-
-// contractions (independent), then the ladders +- with the D slabs
-// (independent); the pack / unpack passes of each block sit between them.
+// scratch slot) through the two independent chains of a pair block, each
+// enqueued on its own stream so that one chain's memory-bound passes run
+// beside the other chain's contractions:
+//   residual chain: g-build -> g+- pack -> ladder +- -> Omega unpack (and E partials)
+//   density chain:  Gamma+- -> slab unpack -> D slabs
+// Each chain has one grouped contraction launch per step for all blocks of the
+// wave.  The chains use disjoint scratch (G, g+-, Omega+- vs Gamma+-, slabs).
 template <typename T>
-static void run_wave(const std::vector<Item>& items, bool do_res, bool do_den, bool do_E, Ctx& c) {
+static void wave_residual(const std::vector<Item>& items, bool do_E, Ctx& c) {
   using S = typename Path<T>::S;
   cudaStream_t st = c.st;
-  std::vector<Gm> first, second;
-  // scratch of an item: slot-part-relative offsets from its own plan
-  auto K = [](const Item& it, size_t off) { return off ? it.slot.scratch + off : nullptr; };
-  auto Q = [](const Item& it, size_t off) { return off ? it.slot.pieces + off : nullptr; };
+  auto K = [](const Item& it, size_t off) { return off ? it.slot.part[1] + off : nullptr; };
+  auto Q = [](const Item& it, size_t off) { return off ? it.slot.part[0] + off : nullptr; };
+  std::vector<Gm> gb, lad;
   for (const Item& it : items) {
     const Plan& P = it.r->P;
     const Ptrs<T> X(*it.r);
     const PBlock& b = P.pbs[it.ib];
     const int v = P.v;
     const int64_t M = static_cast<int64_t>(b.na) * v, N = static_cast<int64_t>(b.nb) * v;
-    if (do_res) {
-      // g-build: G[(b_l,d)][(a_l,c)] = sum_J L^J_ac L^J_bd
-      first.push_back({X.LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, X.LT_piece,
-                       X.LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, X.LT_piece,
-                       M, N, P.Kj, K(it, P.k_G), M, false, X.SC(0), X.SC(0), b.diag ? v : 0});  // diagonal block: a <= b
-    }
-    if (do_den) {
-      // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]
-      first.push_back({X.tpT, P.Kop, P.Pvp, P.Kop, X.tpT_piece, X.bp + b.pair_off * P.Kop, P.Kop, b.npairs, P.Kop,
-                       X.bp_piece, P.Pvp, b.npairs, P.Kop, K(it, P.k_Gp), P.Kvp, false, X.SC(1), X.SC(2)});
-      if (P.minus)
-        first.push_back({X.tmT, P.Kom, P.Pvm, P.Kom, X.tmT_piece, X.bm + b.pair_off * P.Kom, P.Kom, b.npairs, P.Kom,
-                         X.bm_piece, P.Pvm, b.npairs, P.Kom, K(it, P.k_Gm), P.Kvm, false, X.SC(1), X.SC(2)});
-    }
+    // g-build: G[(b_l,d)][(a_l,c)] = sum_J L^J_ac L^J_bd  (diagonal block: only a <= b is read)
+    gb.push_back({X.LT + static_cast<int64_t>(b.a0) * v * P.Kj, P.Kj, M, P.Kj, X.LT_piece,
+                  X.LT + static_cast<int64_t>(b.b0) * v * P.Kj, P.Kj, N, P.Kj, X.LT_piece,
+                  M, N, P.Kj, K(it, P.k_G), M, false, X.SC(0), X.SC(0), b.diag ? v : 0});
   }
-  run_gemms<T>(first.data(), static_cast<int>(first.size()), c);
+  run_gemms<T>(gb.data(), static_cast<int>(gb.size()), c);
   if (c.err) return;  // nothing more is launched after a refused or failed launch
   for (const Item& it : items) {
     const Plan& P = it.r->P;
     const Ptrs<T> X(*it.r);
     const PBlock& b = P.pbs[it.ib];
-    const int v = P.v;
     const unsigned ntp = static_cast<unsigned>(P.nt * (P.nt + 1) / 2);
-    const int64_t gpiece_p = P.maxpairs * P.Kvp, gpiece_m = P.maxpairs * P.Kvm, gt_piece = P.maxrows * P.ldt;
-    if (do_res) {
-      k_pack_g<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
-          reinterpret_cast<const S*>(K(it, P.k_G)), static_cast<int64_t>(b.na) * v, v, b.a0, b.b0, b.nb, b.diag,
-          P.nt, reinterpret_cast<T*>(Q(it, P.k_gp)), P.Kvp, gpiece_p, reinterpret_cast<T*>(Q(it, P.k_gm)), P.Kvm,
-          gpiece_m, P.minus, X.SC(3));
-      c.launched();
-    }
-    if (do_den) {
-      k_unpack_gamma<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
-          reinterpret_cast<const S*>(K(it, P.k_Gp)), reinterpret_cast<const S*>(K(it, P.k_Gm)), P.Kvp, P.Kvm, v, P.vp,
-          b.a0, b.b0, b.nb, b.diag, P.nt, P.minus, reinterpret_cast<T*>(Q(it, P.k_Gt)), P.ldt, gt_piece,
-          reinterpret_cast<T*>(Q(it, P.k_Gb)), P.ldt, gt_piece, X.SC(4));
-      c.launched();
-    }
+    k_pack_g<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
+        reinterpret_cast<const S*>(K(it, P.k_G)), static_cast<int64_t>(b.na) * P.v, P.v, b.a0, b.b0, b.nb, b.diag,
+        P.nt, reinterpret_cast<T*>(Q(it, P.k_gp)), P.Kvp, P.maxpairs * P.Kvp, reinterpret_cast<T*>(Q(it, P.k_gm)),
+        P.Kvm, P.maxpairs * P.Kvm, P.minus, X.SC(3));
+    c.launched();
+    // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]
+    // (the g+- maps end at the last virtual pair: columns up to the padded K read as zero)
+    lad.push_back({Q(it, P.k_gp), P.Kvp, b.npairs, P.Pvp, P.maxpairs * P.Kvp, X.tp, P.Kvp, P.Pop, P.Kvp, X.tp_piece,
+                   b.npairs, P.Pop, P.Kvp, K(it, P.k_Op), P.ldO, false, X.SC(3), X.SC(1)});
+    if (P.minus)
+      lad.push_back({Q(it, P.k_gm), P.Kvm, b.npairs, P.Pvm, P.maxpairs * P.Kvm, X.tm, P.Kvm, P.Pom, P.Kvm,
+                     X.tm_piece, b.npairs, P.Pom, P.Kvm, K(it, P.k_Om), P.ldO, false, X.SC(3), X.SC(1)});
   }
-  for (const Item& it : items) {
-    const Plan& P = it.r->P;
-    const Ptrs<T> X(*it.r);
-    const PBlock& b = P.pbs[it.ib];
-    const int v = P.v, vp = P.vp, nj = P.nj;
-    const int64_t vv = static_cast<int64_t>(v) * v;
-    const int64_t gpiece_p = P.maxpairs * P.Kvp, gpiece_m = P.maxpairs * P.Kvm, gt_piece = P.maxrows * P.ldt;
-    if (do_res) {
-      // ladder: Omega^pm[p][pr] = sum_k g^pm[pr][k] tau^pm[p][k]
-      // (the g+- maps end at the last virtual pair: columns up to the padded K read as zero)
-      second.push_back({Q(it, P.k_gp), P.Kvp, b.npairs, P.Pvp, gpiece_p, X.tp, P.Kvp, P.Pop, P.Kvp, X.tp_piece,
-                        b.npairs, P.Pop, P.Kvp, K(it, P.k_Op), P.ldO, false, X.SC(3), X.SC(1)});
-      if (P.minus)
-        second.push_back({Q(it, P.k_gm), P.Kvm, b.npairs, P.Pvm, gpiece_m, X.tm, P.Kvm, P.Pom, P.Kvm, X.tm_piece,
-                          b.npairs, P.Pom, P.Kvm, K(it, P.k_Om), P.ldO, false, X.SC(3), X.SC(1)});
-    }
-    if (do_den) {
-      // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd  (top and, off the diagonal, bottom)
-      const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 64);
-      const int64_t Mb = static_cast<int64_t>(b.nb) * v, Kb = rup(static_cast<int64_t>(b.na) * vp, 64);
-      // (the slab maps end at the block's last column: the rest of the padded K reads as zero)
-      second.push_back({Q(it, P.k_Gt), P.ldt, Mt, static_cast<int64_t>(b.nb) * vp, gt_piece,
-                        X.LN + static_cast<int64_t>(b.b0) * vp,
-                        static_cast<int64_t>(v) * vp, nj, static_cast<int64_t>(v - b.b0) * vp, X.LN_piece, Mt, nj,
-                        Kt, X.Dacc + static_cast<int64_t>(b.a0) * v, vv, true, X.SC(4), X.SC(0)});
-      if (!b.diag)
-        second.push_back({Q(it, P.k_Gb), P.ldt, Mb, static_cast<int64_t>(b.na) * vp, gt_piece,
-                          X.LN + static_cast<int64_t>(b.a0) * vp,
-                          static_cast<int64_t>(v) * vp, nj, static_cast<int64_t>(v - b.a0) * vp, X.LN_piece, Mb,
-                          nj, Kb, X.Dacc + static_cast<int64_t>(b.b0) * v, vv, true, X.SC(4), X.SC(0)});
-    }
-  }
-  run_gemms<T>(second.data(), static_cast<int>(second.size()), c);
-  if (c.err || !do_res) return;
+  run_gemms<T>(lad.data(), static_cast<int>(lad.size()), c);
+  if (c.err) return;
   for (const Item& it : items) {
     const Plan& P = it.r->P;
     const Ptrs<T> X(*it.r);
@@ -1187,6 +1151,55 @@ static void run_wave(const std::vector<Item>& items, bool do_res, bool do_den, b
         do_E ? X.epart + static_cast<int64_t>(it.ib) * o2 : nullptr);
     c.launched();
   }
+}
+
+template <typename T>
+static void wave_density(const std::vector<Item>& items, Ctx& c) {
+  using S = typename Path<T>::S;
+  cudaStream_t st = c.st;
+  auto K = [](const Item& it, size_t off) { return off ? it.slot.part[3] + off : nullptr; };
+  auto Q = [](const Item& it, size_t off) { return off ? it.slot.part[2] + off : nullptr; };
+  std::vector<Gm> gam, den;
+  for (const Item& it : items) {
+    const Plan& P = it.r->P;
+    const Ptrs<T> X(*it.r);
+    const PBlock& b = P.pbs[it.ib];
+    // Gamma'^pm[pr][k] = sum_p tau^pm^T[k][p] tbar^pm[pr][p]
+    gam.push_back({X.tpT, P.Kop, P.Pvp, P.Kop, X.tpT_piece, X.bp + b.pair_off * P.Kop, P.Kop, b.npairs, P.Kop,
+                   X.bp_piece, P.Pvp, b.npairs, P.Kop, K(it, P.k_Gp), P.Kvp, false, X.SC(1), X.SC(2)});
+    if (P.minus)
+      gam.push_back({X.tmT, P.Kom, P.Pvm, P.Kom, X.tmT_piece, X.bm + b.pair_off * P.Kom, P.Kom, b.npairs, P.Kom,
+                     X.bm_piece, P.Pvm, b.npairs, P.Kom, K(it, P.k_Gm), P.Kvm, false, X.SC(1), X.SC(2)});
+  }
+  run_gemms<T>(gam.data(), static_cast<int>(gam.size()), c);
+  if (c.err) return;
+  for (const Item& it : items) {
+    const Plan& P = it.r->P;
+    const Ptrs<T> X(*it.r);
+    const PBlock& b = P.pbs[it.ib];
+    const int v = P.v, vp = P.vp, nj = P.nj;
+    const int64_t vv = static_cast<int64_t>(v) * v, gt_piece = P.maxrows * P.ldt;
+    const unsigned ntp = static_cast<unsigned>(P.nt * (P.nt + 1) / 2);
+    k_unpack_gamma<T, S><<<dim3(ntp, static_cast<unsigned>(b.npairs)), dim3(32, 8), 0, st>>>(
+        reinterpret_cast<const S*>(K(it, P.k_Gp)), reinterpret_cast<const S*>(K(it, P.k_Gm)), P.Kvp, P.Kvm, v, vp,
+        b.a0, b.b0, b.nb, b.diag, P.nt, P.minus, reinterpret_cast<T*>(Q(it, P.k_Gt)), P.ldt, gt_piece,
+        reinterpret_cast<T*>(Q(it, P.k_Gb)), P.ldt, gt_piece, X.SC(4));
+    c.launched();
+    // D^J_(x,c) += sum_(y,d) Gamma[(x,c)][(y,d)] L^J_yd  (top and, off the diagonal, bottom)
+    // (the slab maps end at the block's last column: the rest of the padded K reads as zero)
+    const int64_t Mt = static_cast<int64_t>(b.na) * v, Kt = rup(static_cast<int64_t>(b.nb) * vp, 64);
+    const int64_t Mb = static_cast<int64_t>(b.nb) * v, Kb = rup(static_cast<int64_t>(b.na) * vp, 64);
+    den.push_back({Q(it, P.k_Gt), P.ldt, Mt, static_cast<int64_t>(b.nb) * vp, gt_piece,
+                   X.LN + static_cast<int64_t>(b.b0) * vp, static_cast<int64_t>(v) * vp, nj,
+                   static_cast<int64_t>(v - b.b0) * vp, X.LN_piece, Mt, nj, Kt, X.Dacc + static_cast<int64_t>(b.a0) * v,
+                   vv, true, X.SC(4), X.SC(0)});
+    if (!b.diag)
+      den.push_back({Q(it, P.k_Gb), P.ldt, Mb, static_cast<int64_t>(b.na) * vp, gt_piece,
+                     X.LN + static_cast<int64_t>(b.a0) * vp, static_cast<int64_t>(v) * vp, nj,
+                     static_cast<int64_t>(v - b.a0) * vp, X.LN_piece, Mb, nj, Kb,
+                     X.Dacc + static_cast<int64_t>(b.b0) * v, vv, true, X.SC(4), X.SC(0)});
+  }
+  run_gemms<T>(den.data(), static_cast<int>(den.size()), c);
 }
 
 // Once per system and call, after its last pair block: D to FP64, E summed.
@@ -1213,61 +1226,115 @@ static double block_weight(const Plan& P, const PBlock& b) {
   return 2.0 * p * v2 * P.nj + 2.0 * lad + 2.0 * P.nj * v2 * rows;
 }
 
+// The density chain's stream: one extra stream per device, created on first
+// use with that device current and kept until the process exits, forked from
+// and joined back to the caller's stream with two events.  A call that uses
+// it holds g_side_mu while it enqueues, so that two host threads never
+// interleave their forks and joins.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static std::mutex g_side_mu;
+static SideStream g_side[64];
+
+static int side_stream(SideStream*& out) {  // caller holds g_side_mu
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CC_ERR_DEVICE;
+  SideStream& ss = g_side[dev];
+  if (!ss.s) {
+    SideStream n;
+    cudaError_t e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      note_cuda(e);
+      return CC_ERR_CUDA;
+    }
+    ss = n;
+  }
+  out = &ss;
+  return CC_OK;
+}
+
 // All systems of a call.  Back to back: each system's pair blocks in order
 // through one slot.  Batched: every system prepared first, then waves that
 // take the next pair block of each of the (up to kBatchSlots) systems with
 // the most work left, so each grouped launch carries the tiles of many
 // systems.  Either way a system's pair blocks run in their own order, so its
-// D accumulates in the same order and the results are the same bits.
+// D accumulates in the same order and the results are the same bits.  With
+// both chains to run, the density chain goes to the side stream (context cd)
+// between a fork after the preparation and a join before the finish.
 template <typename T>
-static void run_all(std::vector<SysRun>& R, const std::vector<Slot>& slots, size_t piece_bytes, bool batched,
-                    bool do_res, bool do_den, bool do_E, Ctx& c) {
+static void run_all(std::vector<SysRun>& R, const std::vector<Slot>& slots, const size_t* part_bytes, bool batched,
+                    bool do_res, bool do_den, bool do_E, Ctx& c, Ctx& cd, const SideStream* side) {
   // The D contraction reads the padding columns inside the Gamma slabs (virtual indices v .. vp-1 of
   // each row block) against zeros of L, which is only harmless if those columns hold finite values:
   // the operand-piece part of every slot starts zeroed, and only piece values (finite) are ever
   // written there, whichever system of the call uses the slot.  (The float-float scratch lives in
   // the other part of the slot, so its bytes are never read as pieces.)
-  for (const Slot& sl : slots) c.cuda(cudaMemsetAsync(sl.pieces, 0, piece_bytes, c.st));
+  for (const Slot& sl : slots) {
+    c.cuda(cudaMemsetAsync(sl.part[0], 0, part_bytes[0], c.st));
+    c.cuda(cudaMemsetAsync(sl.part[2], 0, part_bytes[2], c.st));
+  }
+  Ctx& dc = side ? cd : c;
+  auto fork = [&] {
+    if (!side) return;
+    c.cuda(cudaEventRecord(side->fork, c.st));
+    c.cuda(cudaStreamWaitEvent(side->s, side->fork, 0));
+  };
+  auto join = [&] {
+    if (!side) return;
+    c.cuda(cudaEventRecord(side->join, side->s));
+    c.cuda(cudaStreamWaitEvent(c.st, side->join, 0));
+  };
+  auto wave = [&](const std::vector<Item>& items) {
+    if (do_res && !c.err) wave_residual<T>(items, do_E, c);
+    if (do_den && !dc.err) wave_density<T>(items, dc);
+  };
   if (!batched) {
     for (SysRun& r : R) {
-      if (c.err) return;
+      if (c.err || dc.err) break;
       prep_system<T>(r, do_res, do_den, c);
+      fork();
       if (r.subset.empty()) {
-        for (size_t ib = 0; ib < r.P.pbs.size() && !c.err; ++ib)
-          run_wave<T>({Item{&r, ib, slots[0]}}, do_res, do_den, do_E, c);
+        for (size_t ib = 0; ib < r.P.pbs.size() && !c.err && !dc.err; ++ib) wave({Item{&r, ib, slots[0]}});
       } else {
-        for (size_t k = 0; k < r.subset.size() && !c.err; ++k)
-          run_wave<T>({Item{&r, r.subset[k], slots[0]}}, do_res, do_den, do_E, c);
+        for (size_t k = 0; k < r.subset.size() && !c.err && !dc.err; ++k) wave({Item{&r, r.subset[k], slots[0]}});
       }
-      if (!c.err) finish_system<T>(r, do_res, do_den, do_E, c);
+      join();  // always: the caller's stream must not run ahead of the side stream's work
+      if (!c.err && !dc.err) finish_system<T>(r, do_res, do_den, do_E, c);
     }
-    return;
-  }
-  for (SysRun& r : R) {
-    prep_system<T>(r, do_res, do_den, c);
-    r.next = 0;
-    r.left = 0.0;
-    for (const PBlock& b : r.P.pbs) r.left += block_weight(r.P, b);
-  }
-  std::vector<SysRun*> order;
-  while (!c.err) {
-    order.clear();
-    for (SysRun& r : R)
-      if (r.next < r.P.pbs.size()) order.push_back(&r);
-    if (order.empty()) break;
-    std::stable_sort(order.begin(), order.end(), [](const SysRun* a, const SysRun* b) { return a->left > b->left; });
-    if (order.size() > slots.size()) order.resize(slots.size());
-    std::vector<Item> items;
-    for (size_t k = 0; k < order.size(); ++k) {
-      SysRun* r = order[k];
-      items.push_back(Item{r, r->next, slots[k]});
-      r->left -= block_weight(r->P, r->P.pbs[r->next]);
-      ++r->next;
+  } else {
+    for (SysRun& r : R) {
+      prep_system<T>(r, do_res, do_den, c);
+      r.next = 0;
+      r.left = 0.0;
+      for (const PBlock& b : r.P.pbs) r.left += block_weight(r.P, b);
     }
-    run_wave<T>(items, do_res, do_den, do_E, c);
+    fork();
+    std::vector<SysRun*> order;
+    while (!c.err && !dc.err) {
+      order.clear();
+      for (SysRun& r : R)
+        if (r.next < r.P.pbs.size()) order.push_back(&r);
+      if (order.empty()) break;
+      std::stable_sort(order.begin(), order.end(), [](const SysRun* a, const SysRun* b) { return a->left > b->left; });
+      if (order.size() > slots.size()) order.resize(slots.size());
+      std::vector<Item> items;
+      for (size_t k = 0; k < order.size(); ++k) {
+        SysRun* r = order[k];
+        items.push_back(Item{r, r->next, slots[k]});
+        r->left -= block_weight(r->P, r->P.pbs[r->next]);
+        ++r->next;
+      }
+      wave(items);
+    }
+    join();
+    if (!c.err && !dc.err)
+      for (SysRun& r : R) finish_system<T>(r, do_res, do_den, do_E, c);
   }
-  if (!c.err)
-    for (SysRun& r : R) finish_system<T>(r, do_res, do_den, do_E, c);
+  if (!c.err) c.err = dc.err;
 }
 
 // ---------------------------------------------------------------------------
@@ -1302,16 +1369,15 @@ static int validate(const cc_ladder_system* sys, int n_sys, bool need_tbar) {
 // Batched (CC_WS_BATCH): the header, every system's own region, and
 // min(n_sys, kBatchSlots) slots.  0 on invalid input.
 static size_t ws_need(const cc_ladder_system* sys, int n_sys, int prec, int which) {
-  size_t sys_max = 0, sys_sum = 0, pcs_max = 0, scr_max = 0;
+  size_t sys_max = 0, sys_sum = 0, part_max[4] = {0, 0, 0, 0};
   for (int i = 0; i < n_sys; ++i) {
     Plan P;
     if (!make_plan(sys[i], prec, which, P)) return 0;
     sys_max = std::max(sys_max, P.sys_bytes);
     sys_sum += P.sys_bytes;
-    pcs_max = std::max(pcs_max, P.piece_bytes);
-    scr_max = std::max(scr_max, P.scratch_bytes);
+    for (int q = 0; q < 4; ++q) part_max[q] = std::max(part_max[q], P.part[q]);
   }
-  const size_t slot_max = pcs_max + scr_max;
+  const size_t slot_max = part_max[0] + part_max[1] + part_max[2] + part_max[3];
   if (which & CC_WS_BATCH)
     return kStatusBytes + sys_sum + static_cast<size_t>(std::min(n_sys, kBatchSlots)) * slot_max;
   return kStatusBytes + sys_max + slot_max;
@@ -1346,7 +1412,7 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
   if (clear_status) c.cuda(cudaMemsetAsync(ws, 0, sizeof(Status), c.st));
   std::vector<SysRun> R(n_sys);
   char* w = static_cast<char*>(ws);
-  size_t cur = kStatusBytes, sys_max = 0, pcs_max = 0, scr_max = 0;
+  size_t cur = kStatusBytes, sys_max = 0, part_max[4] = {0, 0, 0, 0};
   for (int i = 0; i < n_sys; ++i) {
     SysRun& r = R[i];
     r.sy = &sys[i];
@@ -1364,22 +1430,36 @@ static int run(const cc_ladder_system* sys, int n_sys, double* const* omega, dou
     r.base = w + (batched ? cur : kStatusBytes);
     cur += r.P.sys_bytes;
     sys_max = std::max(sys_max, r.P.sys_bytes);
-    pcs_max = std::max(pcs_max, r.P.piece_bytes);
-    scr_max = std::max(scr_max, r.P.scratch_bytes);
+    for (int q = 0; q < 4; ++q) part_max[q] = std::max(part_max[q], r.P.part[q]);
   }
-  const size_t slot_bytes = pcs_max + scr_max;
+  const size_t slot_bytes = part_max[0] + part_max[1] + part_max[2] + part_max[3];
   std::vector<Slot> slots;
   char* first = batched ? w + cur : w + kStatusBytes + sys_max;
   for (int k = 0; k < (batched ? std::min(n_sys, kBatchSlots) : 1); ++k) {
-    char* sl = first + static_cast<size_t>(k) * slot_bytes;
-    slots.push_back(Slot{sl, sl + pcs_max});
+    Slot sl;
+    char* at_ = first + static_cast<size_t>(k) * slot_bytes;
+    for (int q = 0; q < 4; ++q) {
+      sl.part[q] = at_;
+      at_ += part_max[q];
+    }
+    slots.push_back(sl);
+  }
+  // with both chains to run, the density chain gets the side stream and its own tile counter
+  std::unique_lock<std::mutex> lk(g_side_mu, std::defer_lock);
+  SideStream* side = nullptr;
+  Ctx cd = c;
+  if (res && den) {
+    lk.lock();
+    if (const int rc2 = side_stream(side)) return rc2;
+    cd.st = side->s;
+    cd.queue = reinterpret_cast<int*>(static_cast<char*>(ws) + kQueueOffset + sizeof(int));
   }
   if (prec == CC_PREC_MIXED)
-    run_all<__nv_bfloat16>(R, slots, pcs_max, batched, res, den, want_E, c);
+    run_all<__nv_bfloat16>(R, slots, part_max, batched, res, den, want_E, c, cd, side);
   else if (prec == CC_PREC_FP16X2)
-    run_all<__half>(R, slots, pcs_max, batched, res, den, want_E, c);
+    run_all<__half>(R, slots, part_max, batched, res, den, want_E, c, cd, side);
   else
-    run_all<double>(R, slots, pcs_max, batched, res, den, want_E, c);
+    run_all<double>(R, slots, part_max, batched, res, den, want_E, c, cd, side);
   return c.err;
 }
 
@@ -2097,13 +2177,34 @@ void cc_ladder_profile(int enable) {
 
 int cc_ladder_profile_read(double* gemm_ms, long long* gemm_launches, double* gemm_flops) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
-  double ms = 0.0;
-  for (auto& pr : g_prof.pending) {
-    if (cudaEventSynchronize(pr.second) != cudaSuccess) return CC_ERR_CUDA;
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess) return CC_ERR_CUDA;
-    ms += t;
+  // contraction launches of the two chains may overlap in time: the time reported is the length
+  // of the union of their [start, end] intervals on a common timeline
+  std::vector<std::pair<double, double>> iv;
+  if (!g_prof.pending.empty()) {
+    cudaEvent_t ref = g_prof.pending.front().first;
+    for (auto& pr : g_prof.pending)
+      if (cudaEventSynchronize(pr.second) != cudaSuccess) return CC_ERR_CUDA;
+    for (auto& pr : g_prof.pending) {
+      float t0 = 0.f, t1 = 0.f;
+      if (cudaEventElapsedTime(&t0, ref, pr.first) != cudaSuccess) return CC_ERR_CUDA;
+      if (cudaEventElapsedTime(&t1, ref, pr.second) != cudaSuccess) return CC_ERR_CUDA;
+      iv.emplace_back(t0, t1);
+    }
   }
+  std::sort(iv.begin(), iv.end());
+  double ms = 0.0, lo = 0.0, hi = 0.0;
+  bool open = false;
+  for (const auto& x : iv) {
+    if (!open || x.first > hi) {
+      if (open) ms += hi - lo;
+      lo = x.first;
+      hi = x.second;
+      open = true;
+    } else {
+      hi = std::max(hi, x.second);
+    }
+  }
+  if (open) ms += hi - lo;
   if (gemm_ms) *gemm_ms = ms;
   if (gemm_launches) *gemm_launches = g_prof.launches;
   if (gemm_flops) *gemm_flops = g_prof.flops;

@@ -93,3 +93,36 @@ def test_autotuner_picks_and_caches(batch, tmp_path):
         assert rel(D[k].cpu(), O.density_rows(s.L_vv, tb2, tt)) < 1e-6
         E_ref = O.lagrangian(tb2, om_ref)
         assert abs(float(E[k]) - E_ref) < 1e-6 * abs(E_ref)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
+def test_batched_schedule_with_more_systems_than_slots(prec):
+    """Eleven systems, eight scratch slots and a small block edge: slots change owner between waves many
+    times while the two chains of a wave run on two streams; the outputs stay the bits of one call per
+    system, and the oracle's."""
+    d = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(d)
+    sizes = [(3, 29, 40), (5, 44, 60), (2, 17, 30), (6, 51, 70), (4, 38, 50), (3, 25, 35), (7, 47, 65),
+             (2, 33, 45), (5, 20, 28), (4, 41, 55), (6, 36, 48)]
+    host, systems = [], []
+    for k, (o, v, nj) in enumerate(sizes):
+        s, tb1, tb2 = synth.make_pair(o, v, nj, 10.0, seed=4400 + k)
+        host.append((s, tb2))
+        systems.append(lad.System(L_vv=t(s.L_vv), t2=t(s.t2), t1=t(s.t1), tbar2=t(tb2), eps=t(s.eps)))
+    try:
+        lad.cc_ladder_set_tuning(12, 0)
+        ws = lad.workspace(systems, prec, batched=True)
+        om, D, E = lad.cc_ladder_step(systems, prec=prec, ws=ws)
+        torch.cuda.synchronize()
+        assert lad.cc_ladder_status(ws) == 0
+        for k, sd in enumerate(systems):
+            om1, D1, E1 = lad.cc_ladder_step([sd], prec=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(om[k], om1[0]) and torch.equal(D[k], D1[0]) and float(E[k]) == float(E1[0]), k
+    finally:
+        lad.cc_ladder_set_tuning(0, 0)
+    for k in range(len(systems)):
+        s, tb2 = host[k]
+        tt = O.tau(s.t1, s.t2)
+        assert rel(om[k].cpu(), O.residual_rows(s.L_vv, tt)) < 1e-6
+        assert rel(D[k].cpu(), O.density_rows(s.L_vv, tb2, tt)) < 1e-6
