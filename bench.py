@@ -48,8 +48,8 @@ PREC = {
 # DRAM bytes of the contraction kernel per step (sum of dram__bytes_read.sum + dram__bytes_write.sum over its
 # launches of one step) from one-pass ncu captures of this kernel version; null for combinations not captured
 TRAFFIC = {
-    ("retinal", "mixed"): (2.465e13, "dram__bytes_read.sum + dram__bytes_write.sum over the 420 launches of one "
-                                     "retinal-scale step, kernel with triangle-skipping g-build"),
+    ("retinal", "mixed"): (2.718e13, "dram__bytes_read.sum + dram__bytes_write.sum over the 420 launches of one "
+                                     "retinal-scale step, persistent grouped kernel (queue-pulled 128x128 tiles)"),
 }
 
 
@@ -426,6 +426,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": PREC[args.prec][1],
             "data": "synthetic (seeded device generator: MP2 amplitudes from random symmetric Cholesky vectors)",
             "config": {"workload": f"{args.workload} o={o} v={v} nj={nj}", "global_batch": world,
+                       "kernel": args.kernel,
                        "parallelism": (f"one system, pair blocks dealt over {world} GPUs (LPT), D by reduce-scatter"
                                        if split else f"independent systems, one per GPU ({world})"),
                        "l2": "inputs larger than L2 (55 GB resident), no flush needed",
@@ -496,7 +497,7 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 split (FP32 accumulate, FP64 reductions)",
         "data": "synthetic (seeded, device generator)",
-        "config": {"workload": "batch24 o~U{6..40} v~U{50..300} nj=5v", "global_batch": 24,
+        "config": {"workload": "batch24 o~U{6..40} v~U{50..300} nj=5v", "global_batch": 24, "kernel": args.kernel,
                    "sizes": sizes, "counted_flops": F, "tuning": tuned},
         "one_call_per_system_ms": ms_seq, "graph_over_one_by_one": ms_seq / ms_graph,
         "graph_equals_one_by_one": same, "clocks": clk.summary(),
@@ -603,12 +604,24 @@ def run_fp64cmp(args):
     with Clocks(0) as clk:
         om64, D64, E64, ms64, st64 = timed_step("fp64", warm=args.workload != "retinal")
     res["fp64"] = {"ms": ms64, "tflops": F / (ms64 * 1e-3) / 1e12, "status": st64}
-    for prec in ("mixed", "fp16x2"):
-        om, D, E, ms, st = timed_step(prec)
-        res[prec] = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12, "status": st, "speedup_over_fp64": ms64 / ms,
-                     "rel_err_omega_vs_fp64": frob(om, om64), "rel_err_D_vs_fp64": frob(D, D64),
-                     "rel_err_E_vs_fp64": abs(E - E64) / abs(E64)}
-        del om, D
+    # each split path at its default leading-product window first, then the other distinct windows
+    # (win_kblocks * 32 K terms, at least one 64-term K step, so 1 and 2 are the same window); the
+    # truncation bias of the FP32 tensor-core accumulation grows with the window
+    for prec, wins in (("mixed", (4, 2, 8)), ("fp16x2", (2, 4))):
+        for i, win in enumerate(wins):
+            lad.cc_ladder_set_tuning(0, win)
+            try:
+                om, D, E, ms, st = timed_step(prec)
+            finally:
+                lad.cc_ladder_set_tuning(0, 0)
+            r = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12, "status": st, "speedup_over_fp64": ms64 / ms,
+                 "rel_err_omega_vs_fp64": frob(om, om64), "rel_err_D_vs_fp64": frob(D, D64),
+                 "rel_err_E_vs_fp64": abs(E - E64) / abs(E64)}
+            del om, D
+            if i == 0:
+                res[prec] = dict(r, win_kblocks=win, by_window={})
+            else:
+                res[prec]["by_window"][str(win)] = r
     line = {"metric": "plain FP64 path useful TFLOP/s; split paths' errors against it (full tensors)",
             "value": res["fp64"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -641,7 +654,13 @@ def main():
     ap.add_argument("--split", action="store_true",
                     help="under torchrun: one system sharded over the ranks by pair blocks (strong scaling) "
                          "instead of one system per rank (weak scaling)")
+    ap.add_argument("--kernel", default="default", choices=["default", "single", "pair"],
+                    help="split paths' contraction kernel: one CTA per 128x128 tile or a two-CTA cluster per "
+                         "256x128 tile (tcgen05 cta_group::2)")
     args = ap.parse_args()
+    if args.kernel != "default" and args.impl != "reference":
+        from paper_2202_02019_gb300 import ladder as lad
+        lad.cc_ladder_set_contraction({"single": lad.CC_KERNEL_SINGLE, "pair": lad.CC_KERNEL_PAIR}[args.kernel])
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

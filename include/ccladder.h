@@ -345,13 +345,31 @@ const char* cc_ladder_strerror(int code);
  *                48).  Sets the scratch size: size workspaces after changing it.
  *   win_kblocks  split paths only: the leading-piece product is re-started every
  *                win_kblocks * 32 K-terms, rounded down to the contraction's
- *                64-term K step (1, 2, 4 or 8; default 4 for CC_PREC_MIXED, 2 for
+ *                64-term K step and at least one step, so 1 and 2 give the same
+ *                window (1, 2, 4 or 8; default 4 for CC_PREC_MIXED, 2 for
  *                CC_PREC_FP16X2).  Smaller windows lower the truncation bias of
  *                the tensor-core FP32 accumulation (retinal-scale system, split
- *                BF16: about 1.8e-7 relative at 2 vs 2.6e-7 at 4) at some speed.
+ *                BF16: about 1.8e-7 relative at 2 vs 2.6e-7 at 4) at some speed;
+ *                8 (256 terms) can exceed 1e-6 (1.09e-6 for Omega at o=6,
+ *                v=157, N_J=300, split BF16). 
  * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
  * on other host threads. */
 int cc_ladder_set_tuning(int block_edge, int win_kblocks);
+
+/* Which tensor-core contraction kernel the split paths use, process-wide, for
+ * calls made afterwards:
+ *   0                 default;
+ *   CC_KERNEL_SINGLE  one CTA per 128 x 128 output tile;
+ *   CC_KERNEL_PAIR    a cluster of two CTAs per 256 x 128 output tile
+ *                     (tcgen05.mma.cta_group::2: each CTA loads its 128 rows of
+ *                     A and half of B; 25 % fewer operand bytes per SM and a
+ *                     deeper load pipeline).
+ * Both form every output element from the same products, windows and folds.
+ * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
+ * on other host threads. */
+#define CC_KERNEL_SINGLE 1
+#define CC_KERNEL_PAIR 2
+int cc_ladder_set_contraction(int kind);
 
 /* Kernel launches issued by the calls above since the library was loaded
  * (a host-side counter). */

@@ -34,12 +34,17 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
 
 // Process-wide tuning (cc_ladder_set_tuning); 0 = default.
-static std::atomic<int> g_tune_block{0}, g_tune_win{0};
+static std::atomic<int> g_tune_block{0}, g_tune_win{0}, g_tune_kernel{0};
 int tuned_win_kb(int dflt) {
   const int w = g_tune_win.load();
   if (w > 0) return w;
   const char* e = std::getenv("CC_WIN_KB");
   return (e && *e) ? std::max(1, std::atoi(e)) : dflt;
+}
+bool tuned_pair_mma() {
+  const int k = g_tune_kernel.load();
+  if (k > 0) return k == CC_KERNEL_PAIR;
+  return false;
 }
 
 static std::mutex g_err_mu;
@@ -2156,6 +2161,12 @@ const char* cc_ladder_strerror(int code) {
 }
 
 long long cc_ladder_launch_count(void) { return g_launches.load(); }
+
+int cc_ladder_set_contraction(int kind) {
+  if (kind != 0 && kind != CC_KERNEL_SINGLE && kind != CC_KERNEL_PAIR) return CC_ERR_ARG;
+  ccl::g_tune_kernel.store(kind);
+  return CC_OK;
+}
 
 int cc_ladder_set_tuning(int block_edge, int win_kblocks) {
   if (block_edge < 0 || (block_edge > 0 && (block_edge % 4 || block_edge > 256))) return CC_ERR_ARG;

@@ -79,5 +79,7 @@ void count_launch(int n = 1);
 // Leading-product window of the mixed contraction, in k-blocks of 32
 // (the tuning knob if set, else `dflt`).
 int tuned_win_kb(int dflt);
+// true: split-operand contractions run on CTA pairs (tcgen05 cta_group::2)
+bool tuned_pair_mma();
 
 }  // namespace ccl

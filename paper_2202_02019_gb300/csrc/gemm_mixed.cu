@@ -156,7 +156,9 @@ __device__ __forceinline__ bool mbar_wait_own(uint64_t* bar, uint32_t parity, ui
   return true;
 }
 
-// Flattened tile t -> (problem, m0, n0); false for a tile the problem skips.
+// Flattened tile t -> (problem, m0, n0) for output tiles TBM rows high; false
+// for a tile the problem skips.
+template <int TBM>
 __device__ __forceinline__ bool decode_tile(const Probs& P, int t, int& pi, int& m0, int& n0) {
   int p = 0;
   while (p + 1 < P.nprob && P.p[p + 1].tile0 <= t) ++p;
@@ -168,7 +170,7 @@ __device__ __forceinline__ bool decode_tile(const Probs& P, int t, int& pi, int&
   const int gsz = min(RASTER_GROUP, pr.mt - gm0);
   const int in_grp = lin - grp * RASTER_GROUP * pr.nt;
   pi = p;
-  m0 = (gm0 + in_grp % gsz) * BM;
+  m0 = (gm0 + in_grp % gsz) * TBM;
   n0 = (in_grp / gsz) * BN;
   if (pr.tri > 0) {
     // rows and columns come in blocks of pr.tri (a symmetric product's pair index): a tile whose
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (;;) {
           const int t = atomicAdd(queue, 1);
           if (t >= P.total) break;
-          if (decode_tile(P, t, pi, m0, n0)) break;
+          if (decode_tile<BM>(P, t, pi, m0, n0)) break;
           pi = -1;
         }
         const int slot = tc % TRING;
@@ -504,6 +506,395 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// CTA-pair variant.  A cluster of two CTAs on two SMs owns a 256 x 128 output
+// tile: the even CTA issues tcgen05.mma.cta_group::2 (M = 256), which reads
+// A from both CTAs' shared memory (128 rows each) and B from both (64 of the
+// 128 columns each), and leaves rows 0-127 of D in the even CTA's TMEM and
+// rows 128-255 in the odd one's.  Per SM this loads 72 KB per BF16 k-block
+// instead of 96 KB and the tensor core reads 6 KB of operands per K=16 step
+// instead of 8 KB, so the smem ring holds three BF16 stages (four FP16 ones)
+// instead of two: more of the load latency is hidden.  The arithmetic of
+// every output element (products, windows, drains, folds) is the single-CTA
+// kernel's.
+//
+// Signalling across the pair uses plain remote arrives and stores (no
+// multicast):
+//   * the even CTA's producer pulls tiles from the queue and writes each into
+//     both CTAs' tile rings; before each k-block it arrives on the odd CTA's
+//     go[s] so that the odd producer may load its halves into stage s; the
+//     loads of both CTAs complete on the even CTA's full[s];
+//   * the MMA commits empty[s], hfull and lfull in the even CTA; its drain
+//     warp 2 relays each hfull / lfull phase to the odd CTA;
+//   * hempty, lempty and tempty live in the even CTA and count the arrivals
+//     of both CTAs' consumers;
+//   * a wait that gives up also raises the other CTA's abort flag.
+constexpr int PAIR_BM = 2 * BM;                 // output rows per pair tile
+constexpr int B_HALF = (BN / 2) * BK * 2;       // 8192 B: one 16-bit piece of a 64 x 64 B half-tile
+constexpr int PAIR_SMEM_BYTES = 221184 + 1024 + 512;  // ring, barriers (< 512 B), 1024-byte alignment
+constexpr int PAIR_TEMPTY = 2 * (1 + NDRAIN);   // tile-ring consumers of both CTAs
+
+template <int NP>
+struct PairStages;
+template <>
+struct PairStages<3> {
+  static constexpr int N = 3;  // 3 x 72 KB
+};
+template <>
+struct PairStages<2> {
+  static constexpr int N = 4;  // 4 x 48 KB
+};
+
+__device__ __forceinline__ bool pair_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint32_t peer_abort,
+                                          uint64_t timeout_ns) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > timeout_ns) {
+      *abort = 1;
+      st_cluster_u32(peer_abort, 1u);
+      return false;
+    }
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    cc_gemm_split3_pair(const __grid_constant__ Probs P, int* __restrict__ queue, Status* st,
+                        unsigned long long timeout_ns) {
+  using SC = Scheme<NP>;
+  constexpr int STAGES = PairStages<NP>::N;
+  constexpr int A_STAGE = NP * A_PIECE, B_STAGE = NP * B_HALF, STAGE = A_STAGE + B_STAGE;
+  static_assert(STAGES * STAGE <= 221184, "pair stages exceed the shared-memory ring");
+  constexpr uint32_t IDESC = NP == 3 ? idesc_bf16_f32(PAIR_BM, BN) : idesc_f16_f32(PAIR_BM, BN);
+  const int WIN_KB = P.win_kb, LWIN = P.lwin;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 221184);
+  uint64_t* go = full + STAGES;
+  uint64_t* empty = go + STAGES;
+  uint64_t* hfull = empty + STAGES;   // [2]
+  uint64_t* hempty = hfull + 2;       // [2]
+  uint64_t* lfull = hempty + 2;       // [1]
+  uint64_t* lempty = lfull + 1;       // [1]
+  uint64_t* tfull = lempty + 1;       // [TRING]
+  uint64_t* tempty = tfull + TRING;   // [TRING]
+  uint64_t* mdone = tempty + TRING;   // [1]  (at most 24 barriers: 192 B)
+  int4* ring = reinterpret_cast<int4*>(smem + 221184 + 256);  // [TRING] (16-byte aligned)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ring + TRING);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool lead = rank == 0;
+  const uint32_t peer = rank ^ 1u;
+  const uint32_t peer_abort = mapa_rank(const_cast<int*>(abort_flag), peer);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);   // the even producer's expect_tx; bytes of both CTAs
+      mbar_init(&go[s], 1);     // one arrive from the even producer per k-block
+      mbar_init(&empty[s], 1);  // one MMA commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&hfull[b], 1);
+      mbar_init(&hempty[b], 2 * NDRAIN);
+    }
+    mbar_init(lfull, 1);
+    mbar_init(lempty, 2 * NDRAIN);
+    for (int r = 0; r < TRING; ++r) {
+      mbar_init(&tfull[r], 1);
+      mbar_init(&tempty[r], PAIR_TEMPTY);
+    }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(tslot, TMEM_COLS);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync_all();  // both CTAs' barriers are initialised before any remote arrive
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;
+      int tc = 0;
+      bool ok = true;
+      if (lead) {
+        while (ok) {
+          int pi = -1, m0 = 0, n0 = 0;
+          for (;;) {
+            const int t = atomicAdd(queue, 1);
+            if (t >= P.total) break;
+            if (decode_tile<PAIR_BM>(P, t, pi, m0, n0)) break;
+            pi = -1;
+          }
+          const int slot = tc % TRING;
+          if (!pair_wait(&tempty[slot], ((tc / TRING) & 1) ^ 1, abort_flag, peer_abort, timeout_ns)) {
+            latch_error(st, kErrTimeout, 206);
+            break;
+          }
+          const int4 e = make_int4(pi, m0, n0, 0);
+          ring[slot] = e;
+          st_cluster_v4(mapa_rank(&ring[slot], peer), e);
+          mbar_arrive(&tfull[slot]);
+          mbar_arrive_cluster(mapa_rank(&tfull[slot], peer));
+          ++tc;
+          if (pi < 0) break;
+          const Prob& pr = P.p[pi];
+          const int nkb = pr.K / BK;
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int s = static_cast<int>(g % STAGES);
+            const uint32_t ph = static_cast<uint32_t>((g / STAGES) & 1);
+            if (!pair_wait(&empty[s], ph ^ 1, abort_flag, peer_abort, timeout_ns)) {
+              latch_error(st, kErrTimeout, 201);
+              ok = false;
+              break;
+            }
+            // the odd CTA may now load its halves of k-block g into its stage s
+            mbar_arrive_cluster(mapa_rank(&go[s], peer));
+            uint8_t* sa = smem + s * STAGE;
+            mbar_expect_tx(&full[s], 2 * STAGE);
+            tma_load_3d_pair(&pr.ta, smem_u32(&full[s]), sa, kb * BK, m0, 0);
+            tma_load_3d_pair(&pr.tb, smem_u32(&full[s]), sa + A_STAGE, kb * BK, n0, 0);
+          }
+        }
+        // copies of both CTAs still in flight (only after an abort) land before either CTA leaves
+        for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+          mbar_wait_own(&full[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1), timeout_ns);
+      } else {
+        while (ok) {
+          const int slot = tc % TRING;
+          if (!pair_wait(&tfull[slot], (tc / TRING) & 1, abort_flag, peer_abort, timeout_ns)) {
+            latch_error(st, kErrTimeout, 207);
+            break;
+          }
+          const int4 e = ring[slot];
+          mbar_arrive_cluster(mapa_rank(&tempty[slot], 0));
+          ++tc;
+          if (e.x < 0) break;
+          const Prob& pr = P.p[e.x];
+          const int nkb = pr.K / BK;
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int s = static_cast<int>(g % STAGES);
+            if (!pair_wait(&go[s], static_cast<uint32_t>((g / STAGES) & 1), abort_flag, peer_abort, timeout_ns)) {
+              latch_error(st, kErrTimeout, 208);
+              ok = false;
+              break;
+            }
+            uint8_t* sa = smem + s * STAGE;
+            const uint32_t bar = mapa_rank(&full[s], 0);
+            tma_load_3d_pair(&pr.ta, bar, sa, kb * BK, e.y + BM, 0);
+            tma_load_3d_pair(&pr.tb, bar, sa + A_STAGE, kb * BK, e.z + BN / 2, 0);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lead && lane == 0) {
+      long long g = 0;  // k-blocks consumed
+      int gw = 0;       // H windows issued (H buffer = gw & 1)
+      int gl = 0;       // L segments issued
+      int tc = 0;
+      bool ok = true;
+      while (ok) {
+        const int slot = tc % TRING;
+        if (!pair_wait(&tfull[slot], (tc / TRING) & 1, abort_flag, peer_abort, timeout_ns)) {
+          latch_error(st, kErrTimeout, 207);
+          break;
+        }
+        const int4 e = ring[slot];
+        mbar_arrive(&tempty[slot]);
+        ++tc;
+        if (e.x < 0) break;
+        const int nkb = P.p[e.x].K / BK;
+        const int nwin = (nkb + WIN_KB - 1) / WIN_KB;
+        for (int w = 0; w < nwin && ok; ++w, ++gw) {
+          const int hb = gw & 1;
+          const uint32_t hcol = hb ? COL_H1 : COL_H0;
+          const bool lseg_start = (w % LWIN) == 0;
+          if (gw >= 2 && !pair_wait(&hempty[hb], ((gw >> 1) - 1) & 1, abort_flag, peer_abort, timeout_ns)) {
+            latch_error(st, kErrTimeout, 204);
+            ok = false;
+            break;
+          }
+          if (lseg_start && gl > 0 && !pair_wait(lempty, (gl - 1) & 1, abort_flag, peer_abort, timeout_ns)) {
+            latch_error(st, kErrTimeout, 205);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int kb_beg = w * WIN_KB, kb_end = min(nkb, (w + 1) * WIN_KB);
+          for (int kb = kb_beg; kb < kb_end; ++kb, ++g) {
+            const int s = static_cast<int>(g % STAGES);
+            const uint32_t ph = static_cast<uint32_t>((g / STAGES) & 1);
+            if (!pair_wait(&full[s], ph, abort_flag, peer_abort, timeout_ns)) {
+              latch_error(st, kErrTimeout, 202);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_base = smem_u32(smem + s * STAGE);
+            const uint32_t b_base = a_base + A_STAGE;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+              const bool first = (kb == kb_beg) && ks == 0;
+#pragma unroll
+              for (int q = 0; q < SC::NPROD; ++q) {
+                int pa, pb;
+                SC::pieces(q, pa, pb);
+                const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
+                const uint64_t bd = sdesc_k_sw128(b_base + pb * B_HALF + ks * 32);
+                if (q == SC::NPROD - 1)
+                  umma_f16_pair(tmem + hcol, ad, bd, IDESC, first ? 0u : 1u);
+                else
+                  umma_f16_pair(tmem + COL_L, ad, bd, IDESC, (first && lseg_start && q == 0) ? 0u : 1u);
+              }
+            }
+            umma_commit_pair(&empty[s]);  // releases the stage (of both CTAs) once its MMAs have read it
+          }
+          if (!ok) break;
+          umma_commit_pair(&hfull[hb]);
+          if ((w + 1) % LWIN == 0 || w == nwin - 1) {
+            umma_commit_pair(lfull);
+            ++gl;
+          }
+        }
+      }
+      // every MMA this thread issued completes before TMEM is released
+      umma_commit_pair(mdone);
+      mbar_wait_own(mdone, 0, timeout_ns);
+    }
+    __syncwarp();
+  } else {
+    // drain warps of both CTAs: as in the single-CTA kernel, on this CTA's 128
+    // rows of the pair tile; the even CTA's warp 2 relays every hfull / lfull
+    // phase to the odd CTA, whose drain warps arrive on the even CTA's
+    // hempty / lempty / tempty
+    const int q = warp & 3;
+    const int cb = ((warp - 2) >> 2) * DCOLS;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    const uint32_t lo_addr = tmem + lane_off + COL_LO + cb;
+    const bool relay = lead && warp == 2 && lane == 0;
+    int gw = 0, gl = 0, tc = 0;
+    bool ok = true;
+    while (ok) {
+      const int slot = tc % TRING;
+      bool got = pair_wait(&tfull[slot], (tc / TRING) & 1, abort_flag, peer_abort, timeout_ns);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      const int4 e = ring[slot];
+      __syncwarp();
+      if (lane == 0) {
+        if (lead)
+          mbar_arrive(&tempty[slot]);
+        else
+          mbar_arrive_cluster(mapa_rank(&tempty[slot], 0));
+      }
+      ++tc;
+      if (e.x < 0) break;
+      const Prob& pr = P.p[e.x];
+      const int nkb = pr.K / BK;
+      const int nwin = (nkb + WIN_KB - 1) / WIN_KB;
+      float acc[DCOLS], HI[DCOLS];
+#pragma unroll
+      for (int j = 0; j < DCOLS; ++j) acc[j] = HI[j] = 0.f;
+      {
+        uint32_t z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) z[j] = 0u;
+#pragma unroll
+        for (int c = 0; c < DCOLS; c += 16) tmem_st16(lo_addr + c, z);
+        tmem_st_wait();
+      }
+      for (int w = 0; w < nwin; ++w, ++gw) {
+        const int hb = gw & 1;
+        got = pair_wait(&hfull[hb], (gw >> 1) & 1, abort_flag, peer_abort, timeout_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        if (relay) mbar_arrive_cluster(mapa_rank(&hfull[hb], 1));
+        tc_fence_after();
+        add_cols(tmem + lane_off + (hb ? COL_H1 : COL_H0) + cb, acc);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (lead)
+            mbar_arrive(&hempty[hb]);
+          else
+            mbar_arrive_cluster(mapa_rank(&hempty[hb], 0));
+        }
+        if ((w + 1) % LWIN == 0 || w == nwin - 1) {
+          got = pair_wait(lfull, gl & 1, abort_flag, peer_abort, timeout_ns);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          if (relay) mbar_arrive_cluster(mapa_rank(lfull, 1));
+          tc_fence_after();
+          add_cols(tmem + lane_off + COL_L + cb, acc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if (lead)
+              mbar_arrive(lempty);
+            else
+              mbar_arrive_cluster(mapa_rank(lempty, 0));
+          }
+          ++gl;
+        }
+        if ((w + 1) % FOLD == 0 || w == nwin - 1) fold_cols(lo_addr, acc, HI);
+      }
+      ok = ok && !*abort_flag;
+      if (!ok) break;
+      const int m0 = e.y + static_cast<int>(rank) * BM, n0 = e.z;
+      const int row = m0 + q * 32 + lane;
+      const float inv = (1.f / ld_scale(pr.sa)) * (1.f / ld_scale(pr.sb));  // powers of two: exact
+#pragma unroll
+      for (int c = 0; c < DCOLS; c += 8) {
+        uint32_t l[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]),
+                       "=r"(l[7])
+                     : "r"(lo_addr + c));
+        tmem_ld_wait();
+        if (row < pr.M) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int n = n0 + cb + c + j;
+            if (n < pr.N) {
+              float2 v = ff_scale(ff_fast_two_sum(HI[c + j], __uint_as_float(l[j])), inv);
+              float2* p = pr.out + static_cast<long long>(n) * pr.ldo + row;
+              if (pr.mode == OUT_FF_ACCUM) v = ff_add(*p, v);
+              *p = v;
+            }
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) latch_error(st, kErrTimeout, 203);
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // the pair's MMAs are done and every copy has landed before TMEM and smem go
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, TMEM_COLS);
+  }
+}
+
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 
 
@@ -547,9 +938,35 @@ int sm_count(int dev) {
   return n;
 }
 
+// Clusters of two CTAs that fit on the device at once (cached per device).
 template <int NP>
+int pair_clusters(int dev) {
+  static std::atomic<int> cache[64];
+  int n = cache[dev].load();
+  if (n > 0) return n;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * 256, 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = PAIR_SMEM_BYTES;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaOccupancyMaxActiveClusters(&n, cc_gemm_split3_pair<NP>, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = sm_count(dev) / 2;
+  }
+  cache[dev].store(n);
+  return n;
+}
+
+template <int NP, bool PAIR>
 int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   static_assert(sizeof(Probs) <= 32000, "launch parameters exceed the kernel parameter limit");
+  constexpr int TBM = PAIR ? PAIR_BM : BM;
   Probs P;
   memset(&P, 0, sizeof(P));
   const CUtensorMapDataType dt = NP == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -573,7 +990,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     if ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.B)) & 15) return -1;
     if ((op.lda | op.ldb | op.a_piece | op.b_piece) & 7) return -1;
     if (!make_map(&pr.ta, op.A, op.a_rows, op.a_cols, op.lda, op.a_piece, BM, NP, NP, dt)) return -4;
-    if (!make_map(&pr.tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, BN, NP, NP, dt)) return -4;
+    if (!make_map(&pr.tb, op.B, op.b_rows, op.b_cols, op.ldb, op.b_piece, PAIR ? BN / 2 : BN, NP, NP, dt)) return -4;
     pr.out = static_cast<float2*>(op.out);
     pr.sa = op.scale_a;
     pr.sb = op.scale_b;
@@ -583,7 +1000,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     pr.K = static_cast<int>(op.K);
     pr.mode = op.mode;
     pr.tri = static_cast<int>(op.tri);
-    pr.mt = static_cast<int>((op.M + BM - 1) / BM);
+    pr.mt = static_cast<int>((op.M + TBM - 1) / TBM);
     pr.nt = static_cast<int>((op.N + BN - 1) / BN);
     pr.tile0 = static_cast<int>(total);
     total += static_cast<int64_t>(pr.mt) * pr.nt;
@@ -597,7 +1014,9 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   static std::atomic<uint64_t> attr_set{0};
   if (!(attr_set.load() & (1ull << dev))) {
     const cudaError_t attr_err =
-        cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        PAIR ? cudaFuncSetAttribute(cc_gemm_split3_pair<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    PAIR_SMEM_BYTES)
+             : cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (attr_err != cudaSuccess) {
       note_cuda(attr_err);
       return -4;
@@ -607,7 +1026,23 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   int* queue = ops[0].queue;
   if (!queue) return -1;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), stream);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && PAIR) {
+    const int64_t clusters = std::min<int64_t>(total, pair_clusters<NP>(dev));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters), 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = PAIR_SMEM_BYTES;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, cc_gemm_split3_pair<NP>, P, queue, ops[0].status, ops[0].timeout_ns);
+    if (e == cudaSuccess) e = cudaPeekAtLastError();
+  } else if (e == cudaSuccess) {
     const int64_t ctas = std::min<int64_t>(total, sm_count(dev));
     cc_gemm_split3_tc<NP><<<static_cast<unsigned>(ctas), NTHREADS, SMEM_BYTES, stream>>>(
         P, queue, ops[0].status, ops[0].timeout_ns);
@@ -627,8 +1062,9 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   if (nops < 1 || nops > MAXP) return -1;
   for (int i = 1; i < nops; ++i)
     if (ops[i].pieces != ops[0].pieces) return -1;
-  if (ops[0].pieces == 3) return launch<3>(ops, nops, stream);
-  if (ops[0].pieces == 2) return launch<2>(ops, nops, stream);
+  const bool pair = tuned_pair_mma();
+  if (ops[0].pieces == 3) return pair ? launch<3, true>(ops, nops, stream) : launch<3, false>(ops, nops, stream);
+  if (ops[0].pieces == 2) return pair ? launch<2, true>(ops, nops, stream) : launch<2, false>(ops, nops, stream);
   return -1;
 }
 

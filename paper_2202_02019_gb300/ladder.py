@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
     lib.cc_ladder_scale_by.restype = I
     lib.cc_ladder_set_tuning.argtypes = [I, I]
     lib.cc_ladder_set_tuning.restype = I
+    lib.cc_ladder_set_contraction.argtypes = [I]
+    lib.cc_ladder_set_contraction.restype = I
     lib.cc_ladder_profile.argtypes = [I]
     lib.cc_ladder_profile.restype = None
     lib.cc_ladder_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -117,7 +119,7 @@ EXPORTS = (
     "cc_ladder_lagrangian", "cc_ladder_step", "cc_ladder_update", "cc_ladder_status",
     "cc_ladder_debug_wait", "cc_ladder_strerror", "cc_ladder_launch_count",
     "cc_ladder_profile", "cc_ladder_profile_read", "cc_ladder_lagrangian_noalloc",
-    "cc_ladder_residual_adjoint", "cc_ladder_set_tuning", "cc_ladder_t1_transform",
+    "cc_ladder_residual_adjoint", "cc_ladder_set_tuning", "cc_ladder_set_contraction", "cc_ladder_t1_transform",
     "cc_ladder_w_backtransform", "cc_ladder_density_es", "cc_ladder_mp2_driver_workspace_size",
     "cc_ladder_mp2_driver", "cc_ladder_iterate_workspace_size", "cc_ladder_iterate",
     "cc_ladder_ov3_workspace_size", "cc_ladder_ov3_gs", "cc_ladder_ov3_es_abci",
@@ -556,3 +558,12 @@ def cc_ladder_ov3_es_abic(L_vv, L_ov, tbar1, L2, t2, R0, R1, R2, prec="mixed", w
 def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):
     """Process-wide tuning knobs (0 = default); see the C header."""
     _check(load().cc_ladder_set_tuning(int(block_edge), int(win_kblocks)))
+
+
+CC_KERNEL_SINGLE, CC_KERNEL_PAIR = 1, 2
+
+
+def cc_ladder_set_contraction(kind: int = 0):
+    """Contraction kernel of the split paths, process-wide: 0 default, CC_KERNEL_SINGLE
+    (one CTA per 128 x 128 tile) or CC_KERNEL_PAIR (two-CTA cluster per 256 x 128 tile)."""
+    _check(load().cc_ladder_set_contraction(int(kind)))

@@ -1,0 +1,85 @@
+"""The CTA-pair contraction kernel (tcgen05.mma.cta_group::2, 256 x 128 tiles
+on a cluster of two CTAs) against the FP64 oracle, on a tiny system (every
+tile mostly padding), a system with several ragged pair-block rows (v = 157)
+at every pair-block edge, and against the single-CTA kernel on the same
+inputs (the two form every element from the same products and windows)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2202_02019_gb300 import ladder as lad
+from paper_2202_02019_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"mixed": 1e-6, "fp16x2": 1e-6}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make(o, v, nj, lam, seed):
+    s, tb1, tb2 = synth.make_pair(o, v, nj, lam, seed=seed)
+    tt = O.tau(s.t1, s.t2)
+    om = O.residual_rows(s.L_vv, tt)
+    D = O.density_rows(s.L_vv, tb2, tt)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sd = lad.System(L_vv=t(s.L_vv), t2=t(s.t2), t1=t(s.t1), tbar2=t(tb2), eps=t(s.eps))
+    return sd, om, D, O.lagrangian(tb2, om)
+
+
+def step(sd, prec, kernel, block=0, win=0):
+    try:
+        lad.cc_ladder_set_contraction(kernel)
+        lad.cc_ladder_set_tuning(block, win)
+        ws = lad.workspace([sd], prec)
+        om, D, E = lad.cc_ladder_step([sd], prec=prec, ws=ws)
+        torch.cuda.synchronize()
+        assert lad.cc_ladder_status(ws) == 0
+    finally:
+        lad.cc_ladder_set_contraction(0)
+        lad.cc_ladder_set_tuning(0, 0)
+    return om[0].cpu(), D[0].cpu(), float(E[0])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
+def test_pair_kernel_tiny_system(prec):
+    sd, om_ref, D_ref, E_ref = make(3, 7, 5, 2.0, seed=11)
+    om, D, E = step(sd, prec, lad.CC_KERNEL_PAIR)
+    assert rel(om, om_ref) < TOL[prec] and rel(D, D_ref) < TOL[prec]
+    assert abs(E - E_ref) / abs(E_ref) < TOL[prec]
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    return make(6, 157, 300, 50.0, seed=2202)
+
+
+@pytest.mark.parametrize("block", [32, 48, 96])
+@pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
+def test_pair_kernel_matches_oracle_and_single_cta(ragged, prec, block):
+    sd, om_ref, D_ref, E_ref = ragged
+    om, D, E = step(sd, prec, lad.CC_KERNEL_PAIR, block)
+    eo, ed, ee = rel(om, om_ref), rel(D, D_ref), abs(E - E_ref) / abs(E_ref)
+    print(f"pair {prec} block {block}: Omega {eo:.2e} D {ed:.2e} E {ee:.2e}")
+    assert eo < TOL[prec] and ed < TOL[prec] and ee < TOL[prec], (eo, ed, ee)
+    om1, D1, E1 = step(sd, prec, lad.CC_KERNEL_SINGLE, block)
+    print(f"pair vs single: Omega {rel(om, om1):.2e} D {rel(D, D1):.2e} E {abs(E - E1) / abs(E1):.2e}")
+    assert rel(om, om1) < 1e-7 and rel(D, D1) < 1e-7
+
+
+@pytest.mark.parametrize("win", [2, 4])
+def test_pair_kernel_windows(ragged, win):
+    sd, om_ref, D_ref, E_ref = ragged
+    om, D, E = step(sd, "mixed", lad.CC_KERNEL_PAIR, 0, win)
+    assert rel(om, om_ref) < 1e-6 and rel(D, D_ref) < 1e-6
+
+
+def test_set_contraction_rejects_unknown_kinds():
+    with pytest.raises(lad.LadderError):
+        lad.cc_ladder_set_contraction(3)
+    lad.cc_ladder_set_contraction(0)
