@@ -217,3 +217,16 @@ def test_pair_block_enumeration_matches_the_shard_plan():
         arrb = (C.c_int32 * max(1, len(bl)))(*bl)
         assert lib.cc_ladder_step_blocks(arr, arrb, len(bl), P(0x8000), P(0x9000), P(0xA000), 1, ws, 1 << 40,
                                          None) == -1
+
+
+def test_tuning_knobs_reject_unknown_values_on_the_host():
+    lib = lad.load()
+    for kind in (3, -1, 7):
+        assert lib.cc_ladder_set_contraction(kind) == -1
+    with pytest.raises(lad.LadderError):
+        lad.cc_ladder_set_contraction(3)
+    for kind in (0, lad.CC_KERNEL_SINGLE, lad.CC_KERNEL_PAIR, 0):
+        assert lib.cc_ladder_set_contraction(kind) == 0
+    for win in (3, 5, 16, -1):
+        assert lib.cc_ladder_set_tuning(0, win) == -1
+    assert lib.cc_ladder_set_tuning(0, 0) == 0

@@ -78,8 +78,3 @@ def test_pair_kernel_windows(ragged, win):
     om, D, E = step(sd, "mixed", lad.CC_KERNEL_PAIR, 0, win)
     assert rel(om, om_ref) < 1e-6 and rel(D, D_ref) < 1e-6
 
-
-def test_set_contraction_rejects_unknown_kinds():
-    with pytest.raises(lad.LadderError):
-        lad.cc_ladder_set_contraction(3)
-    lad.cc_ladder_set_contraction(0)
