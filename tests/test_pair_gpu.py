@@ -78,3 +78,38 @@ def test_pair_kernel_windows(ragged, win):
     om, D, E = step(sd, "mixed", lad.CC_KERNEL_PAIR, 0, win)
     assert rel(om, om_ref) < 1e-6 and rel(D, D_ref) < 1e-6
 
+
+
+BATCH = [(3, 7, 35), (6, 50, 250), (4, 23, 115), (8, 61, 305), (2, 12, 60)]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
+def test_pair_kernel_graph_captured_batch_equals_single_cta_calls(prec):
+    """The batched, graph-captured call on CTA pairs gives the bits of one single-CTA call per system."""
+    systems = []
+    for k, (o, v, nj) in enumerate(BATCH):
+        s, tb1, tb2 = synth.make_pair(o, v, nj, 12.0, seed=3202 + 10 * k)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        systems.append(lad.System(L_vv=t(s.L_vv), t2=t(s.t2), t1=t(s.t1), tbar2=t(tb2), eps=t(s.eps)))
+    om = [torch.empty_like(s.t2) for s in systems]
+    D = [torch.empty_like(s.L_vv) for s in systems]
+    E = torch.empty(len(systems), dtype=torch.float64, device="cuda")
+    try:
+        lad.cc_ladder_set_contraction(lad.CC_KERNEL_PAIR)
+        ws = lad.workspace(systems, prec, batched=True)
+        lad.cc_ladder_step(systems, prec=prec, ws=ws, omega=om, D=D, E=E)   # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            lad.cc_ladder_step(systems, prec=prec, ws=ws, omega=om, D=D, E=E)
+        for x in om + D:
+            x.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert lad.cc_ladder_status(ws) == 0
+    finally:
+        lad.cc_ladder_set_contraction(0)
+    for k, sd in enumerate(systems):
+        o1, D1, E1 = step(sd, prec, lad.CC_KERNEL_SINGLE)
+        assert torch.equal(om[k].cpu(), o1) and torch.equal(D[k].cpu(), D1)
+        assert float(E[k]) == E1
