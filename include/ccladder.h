@@ -351,7 +351,9 @@ const char* cc_ladder_strerror(int code);
  *                the tensor-core FP32 accumulation (retinal-scale system, split
  *                BF16: about 1.8e-7 relative at 2 vs 2.6e-7 at 4) at some speed;
  *                8 (256 terms) can exceed 1e-6 (1.09e-6 for Omega at o=6,
- *                v=157, N_J=300, split BF16). 
+ *                v=157, N_J=300, split BF16), and so can 4 (128 terms) on
+ *                CC_PREC_FP16X2 (1.01e-6 at o=6, v=61, N_J=305) although it
+ *                runs 22 % faster there. 
  * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
  * on other host threads. */
 int cc_ladder_set_tuning(int block_edge, int win_kblocks);
