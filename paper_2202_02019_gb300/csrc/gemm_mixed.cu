@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // every output element (products, windows, drains, folds) is the single-CTA
 // kernel's.
 //
-// Signalling across the pair uses plain remote arrives and stores (no
-// multicast):
+// Signalling across the pair uses plain remote arrives and stores, each
+// addressed to one CTA:
 //   * the even CTA's producer pulls tiles from the queue and writes each into
 //     both CTAs' tile rings; before each k-block it arrives on the odd CTA's
 //     go[s] so that the odd producer may load its halves into stage s; the
