@@ -88,3 +88,27 @@ def test_central_differences_fp64(fd_case):
             g = gT if which == "tau" else gB
             an = g[i, j, c, dd] + (g[j, i, dd, c] if (i, j, c, dd) != (j, i, dd, c) else 0.0)
             assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (which, fd, an)
+
+
+@pytest.mark.parametrize("which", ["L", "tau", "tbar"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_input_gradients(fd_case, prec, which):
+    """Only one input requires grad: the forward takes the residual route when dE/dL is not
+    wanted, and the gradient still matches the oracle."""
+    s, tt, tb2 = fd_case
+    d = torch.device("cuda")
+    L = torch.tensor(s.L_vv, device=d, requires_grad=which == "L")
+    tau = torch.tensor(tt, device=d, requires_grad=which == "tau")
+    tbar = torch.tensor(tb2, device=d, requires_grad=which == "tbar")
+    E = ladder_energy(L, tau, tbar, prec)
+    E.backward()
+    torch.cuda.synchronize()
+    E_ref = O.lagrangian(tb2, O.residual_dense(s.L_vv, tt))
+    assert abs(float(E.detach()) - E_ref) <= TOL[prec] * abs(E_ref)
+    got = {"L": L, "tau": tau, "tbar": tbar}[which].grad.cpu().numpy()
+    ref = {"L": lambda: O.dE_dL_general(s.L_vv, tb2, tt), "tau": lambda: O.dE_dtau(s.L_vv, tb2),
+           "tbar": lambda: O.residual_dense(s.L_vv, tt)}[which]()
+    assert rel(got, ref) < TOL[prec]
+    for name, t in (("L", L), ("tau", tau), ("tbar", tbar)):
+        if name != which:
+            assert t.grad is None
