@@ -343,34 +343,43 @@ const char* cc_ladder_strerror(int code);
 /* Tuning knobs, process-wide, for calls made afterwards (0 = default):
  *   block_edge   virtual rows per pair block (multiple of 4, <= 256; default
  *                48).  Sets the scratch size: size workspaces after changing it.
- *   win_kblocks  split paths only: the leading-piece product is re-started every
- *                win_kblocks * 32 K-terms, rounded down to the contraction's
- *                64-term K step and at least one step, so 1 and 2 give the same
- *                window (1, 2, 4 or 8; default 4 for CC_PREC_MIXED, 2 for
- *                CC_PREC_FP16X2).  Smaller windows lower the truncation bias of
- *                the tensor-core FP32 accumulation (retinal-scale system, split
- *                BF16: about 1.8e-7 relative at 2 vs 2.6e-7 at 4) at some speed;
- *                8 (256 terms) can exceed 1e-6 (1.09e-6 for Omega at o=6,
- *                v=157, N_J=300, split BF16), and so can 4 (128 terms) on
- *                CC_PREC_FP16X2 (1.01e-6 at o=6, v=61, N_J=305) although it
- *                runs 22 % faster there. 
+ *   win_kblocks  split paths, CC_KERNEL_SINGLE and CC_KERNEL_PAIR kernels: the
+ *                leading-piece product is re-started every win_kblocks * 32
+ *                K-terms, rounded down to the contraction's 64-term K step and
+ *                at least one step, so 1 and 2 give the same window (1, 2, 4
+ *                or 8; default 4 for CC_PREC_MIXED, 2 for CC_PREC_FP16X2).
+ *                The CC_KERNEL_KBLOCK_WINDOWS kernel (the CC_PREC_FP16X2
+ *                default) has one window per k-block and ignores it.
+ *                The split paths' error is proportional to the window
+ *                (retinal-scale system, split BF16, E against the FP64 path:
+ *                1.8e-7 at 2, 3.5e-7 at 4, 7.2e-7 at 8); 8 can exceed 1e-6
+ *                (1.09e-6 for Omega at o=6, v=157, N_J=300), and so can 4 on
+ *                CC_PREC_FP16X2 with the single-CTA kernel (1.01e-6 at o=6,
+ *                v=61, N_J=305).
  * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
  * on other host threads. */
 int cc_ladder_set_tuning(int block_edge, int win_kblocks);
 
 /* Which tensor-core contraction kernel the split paths use, process-wide, for
  * calls made afterwards:
- *   0                 default;
+ *   0                 default: CC_KERNEL_SINGLE for CC_PREC_MIXED,
+ *                     CC_KERNEL_KBLOCK_WINDOWS for CC_PREC_FP16X2;
  *   CC_KERNEL_SINGLE  one CTA per 128 x 128 output tile;
  *   CC_KERNEL_PAIR    a cluster of two CTAs per 256 x 128 output tile
  *                     (tcgen05.mma.cta_group::2: each CTA loads its 128 rows of
  *                     A and half of B; 25 % fewer operand bytes per SM and a
- *                     deeper load pipeline).
- * Both form every output element from the same products, windows and folds.
+ *                     deeper load pipeline);
+ *   CC_KERNEL_KBLOCK_WINDOWS  one CTA per 128 x 128 tile, every 64-term
+ *                     k-block its own window holding all its products (the
+ *                     small ones first), three window buffers, one commit per
+ *                     k-block; the window knob does not apply.
+ * The first two form every output element from the same products, windows
+ * and folds (bit-identical results); the third rounds differently.
  * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
  * on other host threads. */
 #define CC_KERNEL_SINGLE 1
 #define CC_KERNEL_PAIR 2
+#define CC_KERNEL_KBLOCK_WINDOWS 3
 int cc_ladder_set_contraction(int kind);
 
 /* Kernel launches issued by the calls above since the library was loaded

@@ -41,11 +41,7 @@ int tuned_win_kb(int dflt) {
   const char* e = std::getenv("CC_WIN_KB");
   return (e && *e) ? std::max(1, std::atoi(e)) : dflt;
 }
-bool tuned_pair_mma() {
-  const int k = g_tune_kernel.load();
-  if (k > 0) return k == CC_KERNEL_PAIR;
-  return false;
-}
+int tuned_contraction() { return g_tune_kernel.load(); }
 
 static std::mutex g_err_mu;
 static std::string g_err_text;
@@ -2163,7 +2159,8 @@ const char* cc_ladder_strerror(int code) {
 long long cc_ladder_launch_count(void) { return g_launches.load(); }
 
 int cc_ladder_set_contraction(int kind) {
-  if (kind != 0 && kind != CC_KERNEL_SINGLE && kind != CC_KERNEL_PAIR) return CC_ERR_ARG;
+  if (kind != 0 && kind != CC_KERNEL_SINGLE && kind != CC_KERNEL_PAIR && kind != CC_KERNEL_KBLOCK_WINDOWS)
+    return CC_ERR_ARG;
   ccl::g_tune_kernel.store(kind);
   return CC_OK;
 }

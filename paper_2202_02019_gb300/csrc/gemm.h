@@ -79,7 +79,8 @@ void count_launch(int n = 1);
 // Leading-product window of the mixed contraction, in k-blocks of 32
 // (the tuning knob if set, else `dflt`).
 int tuned_win_kb(int dflt);
-// true: split-operand contractions run on CTA pairs (tcgen05 cta_group::2)
-bool tuned_pair_mma();
+// contraction kernel of the split paths: 0 default, 1 single CTA, 2 CTA pairs
+// (tcgen05 cta_group::2), 3 single CTA with one window per k-block
+int tuned_contraction();
 
 }  // namespace ccl

@@ -1,4 +1,9 @@
 // Split-operand tensor-core contraction for sm_103a (tcgen05 + TMA + TMEM).
+// Three kernels share the scheme below: cc_gemm_split3_tc (one CTA per 128 x
+// 128 tile, windows of a tunable length, the split-BF16 default),
+// cc_gemm_split3_w1 (one window per 64-term k-block, three window buffers,
+// the split-FP16 default) and cc_gemm_split3_pair (CTA pairs on 256 x 128
+// tiles); each is described where it is defined.
 //
 // Two piece schemes share the kernel.
 //  * NP = 3 (split BF16): every operand element is x = x0 + x1 + x2, three
@@ -507,6 +512,250 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// One-k-block-window variant.  Every 64-term k-block is its own window, and
+// all products of a k-block go into the window's accumulator: the small
+// products first (while it is still small, so their truncation is scaled by
+// their weight), the leading product last.  With no separate L accumulator
+// the TMEM holds three H buffers (H0 [0,128), H1 [128,256), H2 [256,384), LO
+// [384,512)), so the drain of a window has two windows of MMA time before its
+// buffer is needed again, and one commit per k-block (to the window's hfull)
+// both releases the stage and hands the window to the drain warps.  The
+// drain, fold and epilogue are the single-CTA kernel's (FOLD1 windows per
+// fold, the same 4096 terms).
+constexpr int NHBUF = 3;
+constexpr int FOLD1 = 64;
+constexpr uint32_t COL_H2 = 256;
+
+template <int NP>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    cc_gemm_split3_w1(const __grid_constant__ Probs P, int* __restrict__ queue, Status* st,
+                      unsigned long long timeout_ns) {
+  using SC = Scheme<NP>;
+  constexpr int STAGES = SC::STAGES;
+  static_assert(STAGES <= NHBUF, "a stage's release is read from the hfull of its k-block: the next phase of "
+                                 "that barrier needs the k-block being loaded only if STAGES <= NHBUF");
+  constexpr int A_STAGE = NP * A_PIECE, B_STAGE = NP * B_PIECE, STAGE = A_STAGE + B_STAGE;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* hfull = full + STAGES;       // [NHBUF]
+  uint64_t* hempty = hfull + NHBUF;      // [NHBUF]
+  uint64_t* tfull = hempty + NHBUF;      // [TRING]
+  uint64_t* tempty = tfull + TRING;      // [TRING]
+  uint64_t* mdone = tempty + TRING;      // [1]
+  int4* ring = reinterpret_cast<int4*>(smem + STAGES * STAGE + 256);  // [TRING] (16-byte aligned)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ring + TRING);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+    for (int b = 0; b < NHBUF; ++b) {
+      mbar_init(&hfull[b], 1);        // one MMA commit per window (= k-block)
+      mbar_init(&hempty[b], NDRAIN);  // every drain warp
+    }
+    for (int r = 0; r < TRING; ++r) {
+      mbar_init(&tfull[r], 1);
+      mbar_init(&tempty[r], 1 + NDRAIN);
+    }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;  // k-blocks (= windows) issued so far
+      int tc = 0;
+      bool ok = true;
+      while (ok) {
+        int pi = -1, m0 = 0, n0 = 0;
+        for (;;) {
+          const int t = atomicAdd(queue, 1);
+          if (t >= P.total) break;
+          if (decode_tile<BM>(P, t, pi, m0, n0)) break;
+          pi = -1;
+        }
+        const int slot = tc % TRING;
+        if (!mbar_wait_bounded(&tempty[slot], ((tc / TRING) & 1) ^ 1, abort_flag, timeout_ns)) {
+          latch_error(st, kErrTimeout, 306);
+          break;
+        }
+        ring[slot] = make_int4(pi, m0, n0, 0);
+        mbar_arrive(&tfull[slot]);
+        ++tc;
+        if (pi < 0) break;
+        const Prob& pr = P.p[pi];
+        const int nkb = pr.K / BK;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          if (g >= STAGES) {
+            // the stage's previous k-block g - STAGES is done once its window's hfull phase completes
+            const long long q = g - STAGES;
+            if (!mbar_wait_bounded(&hfull[q % NHBUF], static_cast<uint32_t>((q / NHBUF) & 1), abort_flag,
+                                   timeout_ns)) {
+              latch_error(st, kErrTimeout, 301);
+              ok = false;
+              break;
+            }
+          }
+          uint8_t* sa = smem + s * STAGE;
+          mbar_expect_tx(&full[s], STAGE);
+          tma_load_3d(&pr.ta, &full[s], sa, kb * BK, m0, 0);
+          tma_load_3d(&pr.tb, &full[s], sa + A_STAGE, kb * BK, n0, 0);
+        }
+      }
+      for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+        mbar_wait_own(&full[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1), timeout_ns);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long g = 0;
+      int tc = 0;
+      bool ok = true;
+      while (ok) {
+        const int slot = tc % TRING;
+        if (!mbar_wait_bounded(&tfull[slot], (tc / TRING) & 1, abort_flag, timeout_ns)) {
+          latch_error(st, kErrTimeout, 307);
+          break;
+        }
+        const int4 e = ring[slot];
+        mbar_arrive(&tempty[slot]);
+        ++tc;
+        if (e.x < 0) break;
+        const int nkb = P.p[e.x].K / BK;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          const int hb = static_cast<int>(g % NHBUF);
+          if (g >= NHBUF && !mbar_wait_bounded(&hempty[hb], static_cast<uint32_t>(((g / NHBUF) - 1) & 1),
+                                               abort_flag, timeout_ns)) {
+            latch_error(st, kErrTimeout, 304);
+            ok = false;
+            break;
+          }
+          if (!mbar_wait_bounded(&full[s], static_cast<uint32_t>((g / STAGES) & 1), abort_flag, timeout_ns)) {
+            latch_error(st, kErrTimeout, 302);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(smem + s * STAGE);
+          const uint32_t b_base = a_base + A_STAGE;
+          const uint32_t hcol = tmem + static_cast<uint32_t>(hb) * 128u;
+          // small products first (the window's accumulator starts with them), the leading one last
+#pragma unroll
+          for (int q = 0; q < SC::NPROD; ++q) {
+            int pa, pb;
+            SC::pieces(q, pa, pb);
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+              const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
+              const uint64_t bd = sdesc_k_sw128(b_base + pb * B_PIECE + ks * 32);
+              umma_f16(hcol, ad, bd, SC::IDESC, (q == 0 && ks == 0) ? 0u : 1u);
+            }
+          }
+          umma_commit(&hfull[hb]);  // the window is done, and so is its k-block's stage
+        }
+      }
+      umma_commit(mdone);
+      mbar_wait_own(mdone, 0, timeout_ns);
+    }
+    __syncwarp();
+  } else {
+    const int q = warp & 3;
+    const int cb = ((warp - 2) >> 2) * DCOLS;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    const uint32_t lo_addr = tmem + lane_off + COL_LO + cb;
+    long long g = 0;
+    int tc = 0;
+    bool ok = true;
+    while (ok) {
+      const int slot = tc % TRING;
+      bool got = mbar_wait_bounded(&tfull[slot], (tc / TRING) & 1, abort_flag, timeout_ns);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      const int4 e = ring[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[slot]);
+      ++tc;
+      if (e.x < 0) break;
+      const Prob& pr = P.p[e.x];
+      const int nkb = pr.K / BK;
+      float acc[DCOLS], HI[DCOLS];
+#pragma unroll
+      for (int j = 0; j < DCOLS; ++j) acc[j] = HI[j] = 0.f;
+      {
+        uint32_t z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) z[j] = 0u;
+#pragma unroll
+        for (int c = 0; c < DCOLS; c += 16) tmem_st16(lo_addr + c, z);
+        tmem_st_wait();
+      }
+      for (int w = 0; w < nkb; ++w, ++g) {
+        const int hb = static_cast<int>(g % NHBUF);
+        got = mbar_wait_bounded(&hfull[hb], static_cast<uint32_t>((g / NHBUF) & 1), abort_flag, timeout_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        add_cols(tmem + lane_off + static_cast<uint32_t>(hb) * 128u + cb, acc);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&hempty[hb]);
+        if ((w + 1) % FOLD1 == 0 || w == nkb - 1) fold_cols(lo_addr, acc, HI);
+      }
+      ok = ok && !*abort_flag;
+      if (!ok) break;
+      const int m0 = e.y, n0 = e.z;
+      const int row = m0 + q * 32 + lane;
+      const float inv = (1.f / ld_scale(pr.sa)) * (1.f / ld_scale(pr.sb));  // powers of two: exact
+#pragma unroll
+      for (int c = 0; c < DCOLS; c += 8) {
+        uint32_t l[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]),
+                       "=r"(l[7])
+                     : "r"(lo_addr + c));
+        tmem_ld_wait();
+        if (row < pr.M) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int n = n0 + cb + c + j;
+            if (n < pr.N) {
+              float2 v = ff_scale(ff_fast_two_sum(HI[c + j], __uint_as_float(l[j])), inv);
+              float2* p = pr.out + static_cast<long long>(n) * pr.ldo + row;
+              if (pr.mode == OUT_FF_ACCUM) v = ff_add(*p, v);
+              *p = v;
+            }
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) latch_error(st, kErrTimeout, 303);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // CTA-pair variant.  A cluster of two CTAs on two SMs owns a 256 x 128 output
 // tile: the even CTA issues tcgen05.mma.cta_group::2 (M = 256), which reads
 // A from both CTAs' shared memory (128 rows each) and B from both (64 of the
@@ -963,7 +1212,7 @@ int pair_clusters(int dev) {
   return n;
 }
 
-template <int NP, bool PAIR>
+template <int NP, bool PAIR, bool W1 = false>
 int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   static_assert(sizeof(Probs) <= 32000, "launch parameters exceed the kernel parameter limit");
   constexpr int TBM = PAIR ? PAIR_BM : BM;
@@ -1016,6 +1265,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     const cudaError_t attr_err =
         PAIR ? cudaFuncSetAttribute(cc_gemm_split3_pair<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     PAIR_SMEM_BYTES)
+        : W1 ? cudaFuncSetAttribute(cc_gemm_split3_w1<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
              : cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (attr_err != cudaSuccess) {
       note_cuda(attr_err);
@@ -1044,8 +1294,12 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     if (e == cudaSuccess) e = cudaPeekAtLastError();
   } else if (e == cudaSuccess) {
     const int64_t ctas = std::min<int64_t>(total, sm_count(dev));
-    cc_gemm_split3_tc<NP><<<static_cast<unsigned>(ctas), NTHREADS, SMEM_BYTES, stream>>>(
-        P, queue, ops[0].status, ops[0].timeout_ns);
+    if (W1)
+      cc_gemm_split3_w1<NP><<<static_cast<unsigned>(ctas), NTHREADS, SMEM_BYTES, stream>>>(
+          P, queue, ops[0].status, ops[0].timeout_ns);
+    else
+      cc_gemm_split3_tc<NP><<<static_cast<unsigned>(ctas), NTHREADS, SMEM_BYTES, stream>>>(
+          P, queue, ops[0].status, ops[0].timeout_ns);
     e = cudaPeekAtLastError();
   }
   if (e != cudaSuccess) {
@@ -1062,9 +1316,18 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   if (nops < 1 || nops > MAXP) return -1;
   for (int i = 1; i < nops; ++i)
     if (ops[i].pieces != ops[0].pieces) return -1;
-  const bool pair = tuned_pair_mma();
-  if (ops[0].pieces == 3) return pair ? launch<3, true>(ops, nops, stream) : launch<3, false>(ops, nops, stream);
-  if (ops[0].pieces == 2) return pair ? launch<2, true>(ops, nops, stream) : launch<2, false>(ops, nops, stream);
+  // default: the single-CTA kernel for split BF16, one window per k-block for split FP16 (whose
+  // 64-term windows already made the L drain and the double-buffered window handshake its bound)
+  int kind = tuned_contraction();
+  if (kind == 0) kind = ops[0].pieces == 2 ? 3 : 1;
+  if (ops[0].pieces == 3)
+    return kind == 2 ? launch<3, true>(ops, nops, stream)
+         : kind == 3 ? launch<3, false, true>(ops, nops, stream)
+                     : launch<3, false>(ops, nops, stream);
+  if (ops[0].pieces == 2)
+    return kind == 2 ? launch<2, true>(ops, nops, stream)
+         : kind == 3 ? launch<2, false, true>(ops, nops, stream)
+                     : launch<2, false>(ops, nops, stream);
   return -1;
 }
 
