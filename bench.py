@@ -655,14 +655,15 @@ def main():
     ap.add_argument("--split", action="store_true",
                     help="under torchrun: one system sharded over the ranks by pair blocks (strong scaling) "
                          "instead of one system per rank (weak scaling)")
-    ap.add_argument("--kernel", default="default", choices=["default", "single", "pair", "kblock"],
+    ap.add_argument("--kernel", default="default", choices=["default", "single", "pair", "kblock", "pairkblock"],
                     help="split paths' contraction kernel: one CTA per 128x128 tile, a two-CTA cluster per "
                          "256x128 tile (tcgen05 cta_group::2), or one CTA per tile with one window per k-block")
     args = ap.parse_args()
     if args.kernel != "default" and args.impl != "reference":
         from paper_2202_02019_gb300 import ladder as lad
         lad.cc_ladder_set_contraction({"single": lad.CC_KERNEL_SINGLE, "pair": lad.CC_KERNEL_PAIR,
-                                       "kblock": lad.CC_KERNEL_KBLOCK_WINDOWS}[args.kernel])
+                                       "kblock": lad.CC_KERNEL_KBLOCK_WINDOWS,
+                                       "pairkblock": lad.CC_KERNEL_PAIR_KBLOCK_WINDOWS}[args.kernel])
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -372,14 +372,18 @@ int cc_ladder_set_tuning(int block_edge, int win_kblocks);
  *   CC_KERNEL_KBLOCK_WINDOWS  one CTA per 128 x 128 tile, every 64-term
  *                     k-block its own window holding all its products (the
  *                     small ones first), three window buffers, one commit per
- *                     k-block; the window knob does not apply.
- * The first two form every output element from the same products, windows
- * and folds (bit-identical results); the third rounds differently.
+ *                     k-block; the window knob does not apply;
+ *   CC_KERNEL_PAIR_KBLOCK_WINDOWS  the CTA-pair tiles with one window per
+ *                     k-block (three window buffers, three stages).
+ * SINGLE and PAIR form every output element from the same products, windows
+ * and folds (bit-identical results), and so do the two KBLOCK_WINDOWS kinds;
+ * the two groups round differently.
  * Returns CC_ERR_ARG for other values.  Not synchronised with calls in flight
  * on other host threads. */
 #define CC_KERNEL_SINGLE 1
 #define CC_KERNEL_PAIR 2
 #define CC_KERNEL_KBLOCK_WINDOWS 3
+#define CC_KERNEL_PAIR_KBLOCK_WINDOWS 4
 int cc_ladder_set_contraction(int kind);
 
 /* Kernel launches issued by the calls above since the library was loaded

@@ -2159,7 +2159,8 @@ const char* cc_ladder_strerror(int code) {
 long long cc_ladder_launch_count(void) { return g_launches.load(); }
 
 int cc_ladder_set_contraction(int kind) {
-  if (kind != 0 && kind != CC_KERNEL_SINGLE && kind != CC_KERNEL_PAIR && kind != CC_KERNEL_KBLOCK_WINDOWS)
+  if (kind != 0 && kind != CC_KERNEL_SINGLE && kind != CC_KERNEL_PAIR && kind != CC_KERNEL_KBLOCK_WINDOWS &&
+      kind != CC_KERNEL_PAIR_KBLOCK_WINDOWS)
     return CC_ERR_ARG;
   ccl::g_tune_kernel.store(kind);
   return CC_OK;

@@ -524,7 +524,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // fold, the same 4096 terms).
 constexpr int NHBUF = 3;
 constexpr int FOLD1 = 64;
-constexpr uint32_t COL_H2 = 256;
 
 template <int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -811,12 +810,16 @@ __device__ __forceinline__ bool pair_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
-template <int NP>
+// W1: the pair form of cc_gemm_split3_w1 (one window per k-block, three
+// window buffers, one commit per k-block that also releases the stage; three
+// stages so that the stage release can be read from the window's hfull).
+template <int NP, bool W1>
 __global__ void __launch_bounds__(NTHREADS, 1)
     cc_gemm_split3_pair(const __grid_constant__ Probs P, int* __restrict__ queue, Status* st,
                         unsigned long long timeout_ns) {
   using SC = Scheme<NP>;
-  constexpr int STAGES = PairStages<NP>::N;
+  constexpr int STAGES = W1 ? 3 : PairStages<NP>::N;
+  constexpr int NH = W1 ? NHBUF : 2;  // window buffers
   constexpr int A_STAGE = NP * A_PIECE, B_STAGE = NP * B_HALF, STAGE = A_STAGE + B_STAGE;
   static_assert(STAGES * STAGE <= 221184, "pair stages exceed the shared-memory ring");
   constexpr uint32_t IDESC = NP == 3 ? idesc_bf16_f32(PAIR_BM, BN) : idesc_f16_f32(PAIR_BM, BN);
@@ -827,13 +830,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + 221184);
   uint64_t* go = full + STAGES;
   uint64_t* empty = go + STAGES;
-  uint64_t* hfull = empty + STAGES;   // [2]
-  uint64_t* hempty = hfull + 2;       // [2]
-  uint64_t* lfull = hempty + 2;       // [1]
+  uint64_t* hfull = empty + STAGES;   // [NH]
+  uint64_t* hempty = hfull + NH;      // [NH]
+  uint64_t* lfull = hempty + NH;      // [1]
   uint64_t* lempty = lfull + 1;       // [1]
   uint64_t* tfull = lempty + 1;       // [TRING]
   uint64_t* tempty = tfull + TRING;   // [TRING]
-  uint64_t* mdone = tempty + TRING;   // [1]  (at most 24 barriers: 192 B)
+  uint64_t* mdone = tempty + TRING;   // [1]  (at most 25 barriers: 200 B)
   int4* ring = reinterpret_cast<int4*>(smem + 221184 + 256);  // [TRING] (16-byte aligned)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(ring + TRING);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -850,7 +853,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&go[s], 1);     // one arrive from the even producer per k-block
       mbar_init(&empty[s], 1);  // one MMA commit
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NH; ++b) {
       mbar_init(&hfull[b], 1);
       mbar_init(&hempty[b], 2 * NDRAIN);
     }
@@ -904,7 +907,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int kb = 0; kb < nkb; ++kb, ++g) {
             const int s = static_cast<int>(g % STAGES);
             const uint32_t ph = static_cast<uint32_t>((g / STAGES) & 1);
-            if (!pair_wait(&empty[s], ph ^ 1, abort_flag, peer_abort, timeout_ns)) {
+            bool freed;
+            if constexpr (W1) {
+              const long long q = g - STAGES;  // the stage's previous k-block: done when its window is
+              freed = q < 0 || pair_wait(&hfull[q % NH], static_cast<uint32_t>((q / NH) & 1), abort_flag,
+                                         peer_abort, timeout_ns);
+            } else {
+              freed = pair_wait(&empty[s], ph ^ 1, abort_flag, peer_abort, timeout_ns);
+            }
+            if (!freed) {
               latch_error(st, kErrTimeout, 201);
               ok = false;
               break;
@@ -966,6 +977,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++tc;
         if (e.x < 0) break;
         const int nkb = P.p[e.x].K / BK;
+        if constexpr (W1) {
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int s = static_cast<int>(g % STAGES);
+            const int hb = static_cast<int>(g % NH);
+            if (g >= NH && !pair_wait(&hempty[hb], static_cast<uint32_t>(((g / NH) - 1) & 1), abort_flag, peer_abort,
+                                      timeout_ns)) {
+              latch_error(st, kErrTimeout, 204);
+              ok = false;
+              break;
+            }
+            if (!pair_wait(&full[s], static_cast<uint32_t>((g / STAGES) & 1), abort_flag, peer_abort, timeout_ns)) {
+              latch_error(st, kErrTimeout, 202);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_base = smem_u32(smem + s * STAGE);
+            const uint32_t b_base = a_base + A_STAGE;
+            const uint32_t hcol = tmem + static_cast<uint32_t>(hb) * 128u;
+#pragma unroll
+            for (int q = 0; q < SC::NPROD; ++q) {  // small products first, the leading one last
+              int pa, pb;
+              SC::pieces(q, pa, pb);
+#pragma unroll
+              for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint64_t ad = sdesc_k_sw128(a_base + pa * A_PIECE + ks * 32);
+                const uint64_t bd = sdesc_k_sw128(b_base + pb * B_HALF + ks * 32);
+                umma_f16_pair(hcol, ad, bd, IDESC, (q == 0 && ks == 0) ? 0u : 1u);
+              }
+            }
+            umma_commit_pair(&hfull[hb]);  // the window is done, and so is its stage (of both CTAs)
+          }
+          continue;
+        }
         const int nwin = (nkb + WIN_KB - 1) / WIN_KB;
         for (int w = 0; w < nwin && ok; ++w, ++gw) {
           const int hb = gw & 1;
@@ -1067,6 +1112,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c = 0; c < DCOLS; c += 16) tmem_st16(lo_addr + c, z);
         tmem_st_wait();
       }
+      if constexpr (W1) {
+        for (int w = 0; w < nkb; ++w, ++gw) {
+          const int hb = gw % NH;
+          got = pair_wait(&hfull[hb], static_cast<uint32_t>((gw / NH) & 1), abort_flag, peer_abort, timeout_ns);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          if (relay) mbar_arrive_cluster(mapa_rank(&hfull[hb], 1));
+          tc_fence_after();
+          add_cols(tmem + lane_off + static_cast<uint32_t>(hb) * 128u + cb, acc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if (lead)
+              mbar_arrive(&hempty[hb]);
+            else
+              mbar_arrive_cluster(mapa_rank(&hempty[hb], 0));
+          }
+          if ((w + 1) % FOLD1 == 0 || w == nkb - 1) fold_cols(lo_addr, acc, HI);
+        }
+      } else
       for (int w = 0; w < nwin; ++w, ++gw) {
         const int hb = gw & 1;
         got = pair_wait(&hfull[hb], (gw >> 1) & 1, abort_flag, peer_abort, timeout_ns);
@@ -1188,7 +1255,7 @@ int sm_count(int dev) {
 }
 
 // Clusters of two CTAs that fit on the device at once (cached per device).
-template <int NP>
+template <int NP, bool W1>
 int pair_clusters(int dev) {
   static std::atomic<int> cache[64];
   int n = cache[dev].load();
@@ -1204,7 +1271,7 @@ int pair_clusters(int dev) {
   cfg.dynamicSmemBytes = PAIR_SMEM_BYTES;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaOccupancyMaxActiveClusters(&n, cc_gemm_split3_pair<NP>, &cfg) != cudaSuccess || n <= 0) {
+  if (cudaOccupancyMaxActiveClusters(&n, cc_gemm_split3_pair<NP, W1>, &cfg) != cudaSuccess || n <= 0) {
     cudaGetLastError();
     n = sm_count(dev) / 2;
   }
@@ -1263,7 +1330,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   static std::atomic<uint64_t> attr_set{0};
   if (!(attr_set.load() & (1ull << dev))) {
     const cudaError_t attr_err =
-        PAIR ? cudaFuncSetAttribute(cc_gemm_split3_pair<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        PAIR ? cudaFuncSetAttribute(cc_gemm_split3_pair<NP, W1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     PAIR_SMEM_BYTES)
         : W1 ? cudaFuncSetAttribute(cc_gemm_split3_w1<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
              : cudaFuncSetAttribute(cc_gemm_split3_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -1277,7 +1344,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
   if (!queue) return -1;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), stream);
   if (e == cudaSuccess && PAIR) {
-    const int64_t clusters = std::min<int64_t>(total, pair_clusters<NP>(dev));
+    const int64_t clusters = std::min<int64_t>(total, pair_clusters<NP, W1>(dev));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1290,7 +1357,7 @@ int launch(const GemmOp* ops, int nops, cudaStream_t stream) {
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, cc_gemm_split3_pair<NP>, P, queue, ops[0].status, ops[0].timeout_ns);
+    e = cudaLaunchKernelEx(&cfg, cc_gemm_split3_pair<NP, W1>, P, queue, ops[0].status, ops[0].timeout_ns);
     if (e == cudaSuccess) e = cudaPeekAtLastError();
   } else if (e == cudaSuccess) {
     const int64_t ctas = std::min<int64_t>(total, sm_count(dev));
@@ -1323,10 +1390,12 @@ int gemm_mixed(const GemmOp* ops, int nops, cudaStream_t stream) {
   if (ops[0].pieces == 3)
     return kind == 2 ? launch<3, true>(ops, nops, stream)
          : kind == 3 ? launch<3, false, true>(ops, nops, stream)
+         : kind == 4 ? launch<3, true, true>(ops, nops, stream)
                      : launch<3, false>(ops, nops, stream);
   if (ops[0].pieces == 2)
     return kind == 2 ? launch<2, true>(ops, nops, stream)
          : kind == 3 ? launch<2, false, true>(ops, nops, stream)
+         : kind == 4 ? launch<2, true, true>(ops, nops, stream)
                      : launch<2, false>(ops, nops, stream);
   return -1;
 }

@@ -560,11 +560,12 @@ def cc_ladder_set_tuning(block_edge: int = 0, win_kblocks: int = 0):
     _check(load().cc_ladder_set_tuning(int(block_edge), int(win_kblocks)))
 
 
-CC_KERNEL_SINGLE, CC_KERNEL_PAIR, CC_KERNEL_KBLOCK_WINDOWS = 1, 2, 3
+CC_KERNEL_SINGLE, CC_KERNEL_PAIR, CC_KERNEL_KBLOCK_WINDOWS, CC_KERNEL_PAIR_KBLOCK_WINDOWS = 1, 2, 3, 4
 
 
 def cc_ladder_set_contraction(kind: int = 0):
     """Contraction kernel of the split paths, process-wide: 0 default, CC_KERNEL_SINGLE
     (one CTA per 128 x 128 tile), CC_KERNEL_PAIR (two-CTA cluster per 256 x 128 tile) or
-    CC_KERNEL_KBLOCK_WINDOWS (one window per 64-term k-block, three window buffers)."""
+    CC_KERNEL_KBLOCK_WINDOWS (one window per 64-term k-block, three window buffers) or
+    CC_KERNEL_PAIR_KBLOCK_WINDOWS (both)."""
     _check(load().cc_ladder_set_contraction(int(kind)))

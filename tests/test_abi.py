@@ -221,11 +221,11 @@ def test_pair_block_enumeration_matches_the_shard_plan():
 
 def test_tuning_knobs_reject_unknown_values_on_the_host():
     lib = lad.load()
-    for kind in (4, -1, 7):
+    for kind in (5, -1, 7):
         assert lib.cc_ladder_set_contraction(kind) == -1
     with pytest.raises(lad.LadderError):
-        lad.cc_ladder_set_contraction(4)
-    for kind in (0, lad.CC_KERNEL_SINGLE, lad.CC_KERNEL_PAIR, lad.CC_KERNEL_KBLOCK_WINDOWS, 0):
+        lad.cc_ladder_set_contraction(5)
+    for kind in (0, lad.CC_KERNEL_SINGLE, lad.CC_KERNEL_PAIR, lad.CC_KERNEL_KBLOCK_WINDOWS, lad.CC_KERNEL_PAIR_KBLOCK_WINDOWS, 0):
         assert lib.cc_ladder_set_contraction(kind) == 0
     for win in (3, 5, 16, -1):
         assert lib.cc_ladder_set_tuning(0, win) == -1

@@ -1,7 +1,8 @@
-"""The one-window-per-k-block contraction kernel (all products of a 64-term
-k-block in one accumulator, small products first, three window buffers)
-against the FP64 oracle: a tiny system, a system with several ragged
-pair-block rows (v = 157) at several pair-block edges, and a graph-captured
+"""The one-window-per-k-block contraction kernels (all products of a 64-term
+k-block in one accumulator, small products first, three window buffers; one
+CTA per tile or CTA pairs) against the FP64 oracle: a tiny system, a system
+with several ragged pair-block rows (v = 157) at several pair-block edges,
+the pair form against the single-CTA form (bitwise), and a graph-captured
 batch against one call per system (bitwise)."""
 import numpy as np
 import pytest
@@ -33,9 +34,9 @@ def make(o, v, nj, lam, seed):
     return sd, om, D, O.lagrangian(tb2, om)
 
 
-def step(sd, prec, block=0):
+def step(sd, prec, block=0, kernel=K):
     try:
-        lad.cc_ladder_set_contraction(K)
+        lad.cc_ladder_set_contraction(kernel)
         lad.cc_ladder_set_tuning(block, 0)
         ws = lad.workspace([sd], prec)
         om, D, E = lad.cc_ladder_step([sd], prec=prec, ws=ws)
@@ -68,6 +69,16 @@ def test_kblock_windows_match_oracle(ragged, prec, block):
     eo, ed, ee = rel(om, om_ref), rel(D, D_ref), abs(E - E_ref) / abs(E_ref)
     print(f"k-block windows {prec} block {block}: Omega {eo:.2e} D {ed:.2e} E {ee:.2e}")
     assert eo < TOL[prec] and ed < TOL[prec] and ee < TOL[prec], (eo, ed, ee)
+    om2, D2, E2 = step(sd, prec, block, lad.CC_KERNEL_PAIR_KBLOCK_WINDOWS)
+    assert torch.equal(om, om2) and torch.equal(D, D2) and E == E2
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
+def test_pair_kblock_windows_tiny_system(prec):
+    sd, om_ref, D_ref, E_ref = make(3, 7, 5, 2.0, seed=12)
+    om, D, E = step(sd, prec, 0, lad.CC_KERNEL_PAIR_KBLOCK_WINDOWS)
+    assert rel(om, om_ref) < TOL[prec] and rel(D, D_ref) < TOL[prec]
+    assert abs(E - E_ref) / abs(E_ref) < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp16x2"])
