@@ -459,7 +459,9 @@ def run_batch(args):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     F = sum(counted_flops(o, v, nj) for o, v, nj in sizes)
-    tuned = autotune.tune(systems, prec=args.prec, reps=1) if args.autotune else {"block": 0, "win": 0, "source": "default"}
+    tuned = (autotune.tune(systems, prec=args.prec, reps=1, use_cache=False) if args.autotune is not False
+             else {"block": 0, "win": 0, "kernel": 0, "source": "default"})
+    tuned.pop("tried", None)
     ws = lad.workspace(systems, args.prec, batched=True)
     om = [torch.empty_like(s.t2) for s in systems]
     D = [torch.empty_like(s.L_vv) for s in systems]
@@ -646,7 +648,9 @@ def main():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp16x2", "fp64"],
                     help="arithmetic of the timed path (mixed = 3-piece split-BF16)")
     ap.add_argument("--workload", default="retinal", choices=sorted(WORKLOADS) + ["batch24"])
-    ap.add_argument("--autotune", action="store_true", help="batch24: pick tuning knobs with the autotuner")
+    ap.add_argument("--autotune", action="store_true", default=None,
+                    help="pick the tuning knobs (block edge, window, kernel) with the autotuner; the batch24 default")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="batch24: the default knobs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, oracle sample and small-config legs")
     ap.add_argument("--no-small", action="store_true", help="skip the small-config FP64-vs-mixed leg")
     ap.add_argument("--mode", default="step", choices=["step", "autograd", "fp64cmp"],

@@ -76,15 +76,17 @@ def test_autotuner_picks_and_caches(batch, tmp_path):
     host, systems = batch
     path = str(tmp_path / "tune.json")
     try:
-        r = autotune.tune(systems[:3], prec="mixed", candidates=((48, 4), (32, 2)), path=path)
-        assert r["source"] == "measured" and (r["block"], r["win"]) in ((48, 4), (32, 2))
+        cands = ((48, 4, lad.CC_KERNEL_SINGLE), (32, 2, lad.CC_KERNEL_SINGLE), (48, 0, lad.CC_KERNEL_KBLOCK_WINDOWS))
+        r = autotune.tune(systems[:3], prec="mixed", candidates=cands, path=path)
+        assert r["source"] == "measured" and (r["block"], r["win"], r["kernel"]) in cands
         assert os.path.exists(path)
         r2 = autotune.tune(systems[:3], prec="mixed", path=path)
-        assert r2["source"] == "cache" and (r2["block"], r2["win"]) == (r["block"], r["win"])
+        assert r2["source"] == "cache" and (r2["block"], r2["win"], r2["kernel"]) == (r["block"], r["win"], r["kernel"])
         om, D, E = lad.cc_ladder_step(systems[:3], prec="mixed")      # runs with the tuned knobs
         torch.cuda.synchronize()
     finally:
         lad.cc_ladder_set_tuning(0, 0)
+        lad.cc_ladder_set_contraction(0)
     for k in range(3):
         s, tb2 = host[k]
         tt = O.tau(s.t1, s.t2)
